@@ -1,0 +1,404 @@
+#!/usr/bin/env python3
+"""EventTracer hot path on GB300: seconds of 720p, 1 kHz event video per wall-minute.
+
+Workload (the full-pipeline configuration): a ~500k-triangle procedural city
+block (boxes on a street grid, 4 quad lights, environment 0.1), a camera
+moving forward at 10 m/s rendered at 1280x720 and 1000 frames/s, 2 samples per
+pixel, paths of up to 5 segments; every frame's Eq. 1 log luminance feeds the
+EvSNet + BiLIF kernel, which emits the ON/OFF events.  One step = FRAMES
+consecutive frames (FRAMES ms of video) rendered and converted to events; steps
+continue along the camera path, with the EvSNet state carried across steps.
+
+Reported next to it: the 256-SPP + contrast-threshold path on the same GPU and
+kernels (the metric's baseline), event F1 of the method against it, the render
+kernel's roofline fraction, an end-to-end number through the public API with
+host buffers, and the CPU oracle timed on the host cores.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "720p 1kHz event-video s/min vs 256spp+threshold on same GB300 at event F1>=0.9"
+UNIT = "video-s/min"
+W_, H_ = 1280, 720
+DEPTH = 5
+SEED = 0
+C_THR = 0.2
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--frames", type=int, default=50, help="frames per step")
+    p.add_argument("--spp", type=int, default=2)
+    p.add_argument("--baseline-frames", type=int, default=12)
+    p.add_argument("--no-baseline", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--cpu-rows", type=int, default=96, help="oracle sample: rows of one frame")
+    return p.parse_args()
+
+
+def load_net(dtype):
+    """Trained EvSNet weights if present, else random-init weights of the same shape."""
+    import numpy as np
+    from paper_2508_18071_gb300 import api, inputs
+    path = os.path.join(ROOT, "paper_2508_18071_gb300", "weights", "evsnet_city.npz")
+    if os.path.exists(path):
+        z = np.load(path)
+        d = {k: (z[k].item() if z[k].ndim == 0 else z[k]) for k in z.files}
+        d["trained"] = True
+    else:
+        d = inputs.random_evsnet(0, 4, 16, 1, 3, seed=12, vth=0.5, beta=0.9)
+        d["trained"] = False
+    return api.EvsNetDev.from_dict(d, dtype), d
+
+
+class Clocks:
+    def __init__(self, out):
+        self.out = out
+        self.p = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.out, "w")
+            self.p = subprocess.Popen(["nvidia-smi", "--query-gpu=" + q, "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+            self.f.close()
+
+    def summary(self, dev_index=0):
+        if self.p is None or not os.path.exists(self.out):
+            return None
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.out):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9 or not f[0].isdigit() or int(f[0]) != dev_index:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(scene, net_d, spp, rows, frames_for_render=1):
+    """The oracle, as it stands, on a bounded sample of the workload, extrapolated."""
+    import numpy as np
+    import oracle
+    from paper_2508_18071_gb300 import inputs
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    t0 = time.perf_counter()
+    o = oracle.Scene(scene["tris"], scene["tri_mat"], scene["materials"], scene["lights"], scene["env"])
+    t_bvh = time.perf_counter() - t0
+    cams = inputs.city_path(1, first=500)
+    step = max(1, H_ // rows)
+    ys = list(range(0, H_, step))[:rows]
+    t_r = 0.0
+    work = np.zeros(3)
+    for y in ys:
+        t0 = time.perf_counter()
+        o.render(cams, W_, H_, spp, DEPTH, SEED, first_frame=500, rows=(y, y + 1), nthreads=cores)
+        t_r += time.perf_counter() - t0
+        work += [o.rays_traced, o.node_visits, o.tri_tests]
+    t_frame_render = t_r * H_ / len(ys)
+    # EvSNet on a 128x128 crop for 8 steps, extrapolated per 720p frame
+    onet = oracle.EvsNet(net_d["kind"], net_d["n_layers"], net_d["C"], net_d["kt"], net_d["ks"],
+                         net_d["beta"], net_d["vth"], net_d["reset"],
+                         np.asarray(net_d["w"], float), np.asarray(net_d["b"], float))
+    lf = inputs.random_logl_clip(0, 9, 128, 128)
+    st = oracle.EvsState.new(onet, 128, 128)
+    t0 = time.perf_counter()
+    oracle.evsnet_forward(lf, onet, st, nthreads=cores)
+    t_e = time.perf_counter() - t0
+    t_frame_evs = t_e / 8 * (W_ * H_) / (128 * 128)
+    sec_per_video_s = 1000.0 * (t_frame_render + t_frame_evs)
+    samples = len(ys) * W_ * spp
+    return {
+        "value": 60.0 / sec_per_video_s, "unit": UNIT, "cores": cores, "kind": "oracle",
+        "sample": "%d rows x 1280 px x %d spp of one frame rendered (%.1f s) + EvSNet on 128x128 x 8 "
+                  "steps (%.1f s), extrapolated to 1000 frames of 1280x720; BVH build %.1f s excluded"
+                  % (len(ys), spp, t_r, t_e, t_bvh),
+        "_work": {"rays_per_sample": work[0] / samples,
+                  "flops_per_ray": (24.0 * work[1] + 40.0 * work[2]) / max(work[0], 1),
+                  "bytes_per_ray": (64.0 * work[1] + 36.0 * work[2]) / max(work[0], 1)},
+    }
+
+
+def run_reference(args):
+    """--impl reference: the oracle (FP64 CPU) timed on the same workload, one bounded sample per step."""
+    import numpy as np
+    import oracle
+    from paper_2508_18071_gb300 import inputs
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    scene = inputs.city_block(seed=21)
+    o = oracle.Scene(scene["tris"], scene["tri_mat"], scene["materials"], scene["lights"], scene["env"])
+    _, net_d = load_net_host()
+    onet = oracle.EvsNet(net_d["kind"], net_d["n_layers"], net_d["C"], net_d["kt"], net_d["ks"],
+                         net_d["beta"], net_d["vth"], net_d["reset"],
+                         np.asarray(net_d["w"], float), np.asarray(net_d["b"], float))
+    rows_per_step = 4
+    times = []
+    for s in range(args.warmup + args.steps):
+        f = 500 + s
+        cams = inputs.city_path(1, first=f)
+        y0 = (s * 97) % (H_ - rows_per_step)
+        t0 = time.perf_counter()
+        o.render(cams, W_, H_, args.spp, DEPTH, SEED, first_frame=f, rows=(y0, y0 + rows_per_step),
+                 nthreads=cores)
+        t_r = time.perf_counter() - t0
+        lf = inputs.random_logl_clip(s, 3, 64, 64)
+        st = oracle.EvsState.new(onet, 64, 64)
+        t0 = time.perf_counter()
+        oracle.evsnet_forward(lf, onet, st, nthreads=cores)
+        t_e = time.perf_counter() - t0
+        per_frame = t_r * H_ / rows_per_step + t_e / 2 * (W_ * H_) / (64 * 64)
+        if s >= args.warmup:
+            times.append(per_frame)
+    per_frame = statistics.mean(times)
+    value = 60.0 / (1000.0 * per_frame)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_frame * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "city block ~500k tris, 1280x720, 1 kHz, %d spp, depth 5, "
+                       "EvSNet 4x conv3x3 C16 + BiLIF" % args.spp},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "per step: %d rows x 1280 px of one frame + EvSNet 64x64 x 2 "
+                                       "steps, extrapolated to one 720p frame; 1000 frames per "
+                                       "video-second" % rows_per_step},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def load_net_host():
+    import numpy as np
+    from paper_2508_18071_gb300 import inputs
+    path = os.path.join(ROOT, "paper_2508_18071_gb300", "weights", "evsnet_city.npz")
+    if os.path.exists(path):
+        z = np.load(path)
+        d = {k: (z[k].item() if z[k].ndim == 0 else z[k]) for k in z.files}
+        return None, d
+    return None, inputs.random_evsnet(0, 4, 16, 1, 3, seed=12, vth=0.5, beta=0.9)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_2508_18071_gb300 import api, inputs, _lib
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    props = torch.cuda.get_device_properties(dev)
+
+    scene = inputs.city_block(seed=21)
+    g = api.Scene(scene)
+    info = g.info()
+    dtype = _lib.ET_F32
+    net, net_d = load_net(dtype)
+    F = args.frames
+    npix = W_ * H_
+    # weak scaling: every rank renders its own segment of the camera path
+    first = 1000 * rank
+    path = inputs.city_path(F * (args.warmup + args.steps) + 1, first=first)
+    logl = torch.empty((F, H_, W_), dtype=torch.float32, device=dev)
+    state = api.EvsStateDev(net, H_, W_)
+    buf = api.EventBuffer(F * npix)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(k, ev_r=None):
+        f0 = first + k * F
+        cams = path[k * F:(k + 1) * F]
+        if ev_r is not None:
+            ev_r[0].record(stream)
+        api.render_frames(g, cams, W_, H_, args.spp, DEPTH, SEED, first_frame=f0, logl=logl,
+                          want_rgb=False)
+        if ev_r is not None:
+            ev_r[1].record(stream)
+        api.evsnet_forward(logl, net, state, t0=f0, buf=buf)
+        if ev_r is not None:
+            ev_r[2].record(stream)
+
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize()
+    n_ev_warm = buf.n()
+    if world > 1:
+        dist.barrier()
+    evs = []
+    out_dir = os.path.join(ROOT, "gpurun_out")
+    clk = Clocks(os.path.join(out_dir if os.path.isdir(out_dir) else "/tmp", "clocks_bench.csv"))
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    with clk:
+        for k in range(args.warmup, args.warmup + args.steps):
+            flush.zero_()
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            step(k, e)
+            evs.append(e)
+        torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if world > 1:
+        dist.barrier()
+    t_steps = [e[0].elapsed_time(e[2]) for e in evs]
+    t_render = [e[0].elapsed_time(e[1]) for e in evs]
+    t_evs = [e[1].elapsed_time(e[2]) for e in evs]
+    total_ms = sum(t_steps)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    n_ev_last = buf.n()
+    video_s = world * args.steps * F / 1000.0
+    value = video_s / (total_ms / 1000.0 / 60.0)
+
+    # ---- end to end through the public API: host cameras in, events to host out
+    pinned = torch.empty((F * npix, 3), dtype=torch.int32, pin_memory=True)
+    cnt_host = torch.empty(1, dtype=torch.int64, pin_memory=True)
+    e2e_t, d2h = [], []
+    state_e = api.EvsStateDev(net, H_, W_)
+    for k in range(args.warmup + args.steps):
+        f0 = first + k * F
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        api.render_frames(g, path[k * F:(k + 1) * F], W_, H_, args.spp, DEPTH, SEED,
+                          first_frame=f0, logl=logl, want_rgb=False)
+        api.evsnet_forward(logl, net, state_e, t0=f0, buf=buf)
+        cnt_host.copy_(buf.count, non_blocking=True)
+        torch.cuda.synchronize()
+        n = min(int(cnt_host.item()), buf.cap)
+        pinned[:n].copy_(buf.raw[:n], non_blocking=True)
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            e2e_t.append(time.perf_counter() - t0)
+            d2h.append(12 * n + 8)
+    e2e_value = world * args.steps * F / 1000.0 / (sum(e2e_t) / 60.0)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 render + %s EvSNet" % ("f32" if dtype == _lib.ET_F32 else "bf16"),
+        "data": "synthetic (procedural city block, random-init EvSNet)" if not net_d.get("trained")
+                else "synthetic (procedural city block, EvSNet trained on procedural clips)",
+        "config": {"workload": "city block %d tris (BVH %d nodes), 1280x720, 1 kHz, %d spp, depth 5, "
+                               "EvSNet %d x conv%dx%d C%d + BiLIF" % (info["n_tris"], info["n_nodes"],
+                                                                       args.spp, net.n_layers, net.ks,
+                                                                       net.ks, net.C),
+                   "frames_per_step": F, "l2": "flushed between steps (256 MB write)",
+                   "parallelism": "replicas: each rank renders its own path segment"},
+        "wall_s_timed": wall,
+        "gpu_launches": 2 * args.steps,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 52 * F,
+                "d2h_bytes_per_step": int(statistics.mean(d2h))},
+        "events_per_step": (n_ev_last - 0) if n_ev_last <= buf.cap else None,
+        "render_ms_per_frame": statistics.mean(t_render) / F,
+        "evsnet_ms_per_frame": statistics.mean(t_evs) / F,
+        "clocks": clk.summary(local),
+    }
+    if rank != 0:
+        return
+
+    # ---- CPU oracle on a bounded sample (also yields the algorithmic work per ray)
+    cpu = None
+    if not args.no_cpu:
+        cpu = cpu_baseline(scene, net_d, args.spp, args.cpu_rows)
+        work = cpu.pop("_work")
+        line["cpu_baseline"] = cpu
+        flops_launch = work["flops_per_ray"] * work["rays_per_sample"] * npix * args.spp * F
+        t_launch = statistics.mean(t_render) / 1e3
+        peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * 2.07e9 / 1e12
+        line["roofline"] = {"bound": "alu", "achieved": flops_launch / t_launch / 1e12,
+                            "peak": peak, "unit": "TFLOP/s",
+                            "frac": flops_launch / t_launch / 1e12 / peak, "traffic": None,
+                            "kernel": "render_kernel",
+                            "work": "24 flop per BVH node visit + 40 per triangle test, counted by "
+                                    "the oracle's full-sweep SAH BVH on the sampled rays (%.1f "
+                                    "rays/sample, %.0f flop/ray)" % (work["rays_per_sample"],
+                                                                     work["flops_per_ray"]),
+                            "peak_source": "%d SMs x 128 FP32 lanes x 2 x 2.07 GHz (recipe unit "
+                                           "counts and max clock)" % props.multi_processor_count}
+
+    # ---- the metric's baseline: 256 spp + contrast threshold, same kernels
+    if not args.no_baseline:
+        nb = args.baseline_frames
+        bpath = inputs.city_path(nb, first=first + 10000)
+        lb = torch.empty((nb, H_, W_), dtype=torch.float32, device=dev)
+        ref = torch.zeros(npix, dtype=torch.float64, device=dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        api.render_frames(g, bpath, W_, H_, 256, DEPTH, SEED, first_frame=first + 10000, logl=lb,
+                          want_rgb=False)
+        bbuf = api.threshold_events(lb, C_THR, ref, False, t0=first + 10000)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_b = e0.elapsed_time(e1) / 1e3
+        base_value = (nb / 1000.0) / (t_b / 60.0)
+        ref_ev = bbuf.host()
+        # the method on the same frames (fresh state) and the method without EvSNet
+        lm = torch.empty((nb, H_, W_), dtype=torch.float32, device=dev)
+        api.render_frames(g, bpath, W_, H_, args.spp, DEPTH, SEED, first_frame=first + 10000,
+                          logl=lm, want_rgb=False)
+        st2 = api.EvsStateDev(net, H_, W_)
+        m_ev = api.evsnet_forward(lm, net, st2, t0=first + 10000)[0].host()
+        ref2 = torch.zeros(npix, dtype=torch.float64, device=dev)
+        t_ev = api.threshold_events(lm, C_THR, ref2, False, t0=first + 10000).host()
+        line["baseline_256spp_threshold"] = {
+            "value": base_value, "unit": UNIT, "frames_measured": nb,
+            "speedup_of_method": value / base_value}
+        line["event_f1_vs_baseline"] = {
+            "delta_frames": 1, "frames": nb - 1, "method": api.event_f1(m_ev, ref_ev, 1),
+            "threshold_on_low_spp": api.event_f1(t_ev, ref_ev, 1),
+            "n_ref": len(ref_ev), "n_method": len(m_ev), "n_threshold_low_spp": len(t_ev),
+            "gate_0.9_met": api.event_f1(m_ev, ref_ev, 1) >= 0.9}
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,187 @@
+/*
+ * eventtracer.h -- C ABI of libeventtracer, a GB300 (sm_103a) implementation of
+ * the EventTracer hot path (arXiv 2508.18071): path tracing of every frame of a
+ * 1 kHz camera path through a triangle scene, then the EvSNet spiking network
+ * (convolutions + bipolar leaky integrate-and-fire) that turns the noisy frames
+ * into ON/OFF events (t, x, y, p).
+ *
+ * The problem statement these calls follow is the paper's Sec. 3.2: time is cut
+ * into K = T * F_evt steps, a frame I_k is rendered at every t_k = k / F_evt,
+ * each pixel's log-luminance sequence is differenced (Eq. 1) and EvSNet
+ * (Eq. 5-6, BiLIF of Eq. 2-3) emits the events of Sec. 3.1.
+ *
+ * Conventions for every call:
+ *  - Return value: ET_OK or an ET_ERR_* code; et_status_str() names it.  Argument
+ *    errors are detected on the host before anything is enqueued.
+ *  - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy default
+ *    stream).  Device outputs are valid once the stream has been synchronised.
+ *  - The caller owns every input and output buffer.  Buffers marked "device" are
+ *    device pointers (e.g. torch tensors' data_ptr()); "host" are host pointers.
+ *    The library owns only an et_scene and the device memory it holds.
+ *  - Event outputs: the call writes the event count to the device int64
+ *    `*n_events` (the library zeroes it first).  If more than `cap` events were
+ *    produced, only `cap` are stored and *n_events is the full count: the caller
+ *    compares after synchronising and retries with a larger buffer.
+ *  - Events are emitted in no particular order.
+ *  - No call allocates device memory except et_build_scene and the training
+ *    workspace query / et_train_* calls that say so.
+ */
+#ifndef EVENTTRACER_H
+#define EVENTTRACER_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  ET_OK = 0,
+  ET_ERR_ARG = 1,            /* bad argument (null pointer, size out of range)     */
+  ET_ERR_CUDA = 2,           /* a CUDA runtime call or kernel launch failed        */
+  ET_ERR_OOM = 3,            /* device allocation failed                           */
+  ET_ERR_CAPACITY = 4,       /* host-synchronous calls only: output buffer too small */
+  ET_ERR_TIMEOUT = 5,        /* a bounded device-side wait gave up                 */
+  ET_ERR_UNIMPLEMENTED = 6   /* configuration not supported by this build          */
+};
+
+enum { ET_LAMBERT = 0, ET_GGX = 1 };
+enum { ET_LOG_EPS = 0,       /* l = ln(L + eps)                           (default) */
+       ET_LOG_PAPER = 1 };   /* Eq. 1 as printed: ln L if L >= rho else (ln rho / rho) L */
+enum { ET_F32 = 0, ET_BF16 = 1, ET_FP8 = 2 };
+enum { ET_NET_STACK = 0,     /* plain stack of conv + ReLU layers                   */
+       ET_NET_RESIDUAL = 1 };/* Eq. 5: encoder conv + M residual blocks            */
+
+typedef struct et_scene et_scene;
+
+/* Material: albedo (Lambert) or Schlick F0 (GGX); GGX alpha = roughness. */
+typedef struct { float albedo[3]; float roughness; int32_t type; } et_material;
+
+/* One-sided parallelogram light: points p0 + u e1 + v e2, (u, v) in [0,1)^2, emitting
+ * radiance on the side of e1 x e2.  et_build_scene appends its two triangles
+ * (p0, p0+e1, p0+e1+e2) and (p0, p0+e1+e2, p0+e2) to the geometry. */
+typedef struct { float p0[3], e1[3], e2[3]; float radiance[3]; } et_quad_light;
+
+/* Pinhole camera: position, camera-to-world rotation stored row-major whose
+ * columns are the camera's right, up and backward axes, vertical FOV (degrees). */
+typedef struct { float pos[3]; float rot[9]; float vfov_deg; } et_camera;
+
+/* Event (Sec. 3.1): pixel (x, y), frame index t (time t / F_evt), polarity +-1. */
+typedef struct { uint16_t x, y; uint32_t t; int8_t p; uint8_t pad[3]; } et_event;
+
+/* ---------------------------------------------------------------------- scene
+ * Builds the scene: copies the geometry to the device and builds a binned-SAH
+ * bounding volume hierarchy (two-wide, leaves of at most 4 triangles).
+ *   tris      host float [n_tris][9]: v0, v1, v2 of each triangle
+ *   tri_mat   host uint32 [n_tris]: material index (< n_mats)
+ *   mats      host [n_mats];  lights host [n_lights] (may be 0)
+ *   env       radiance of the constant environment seen by rays that miss
+ * Allocates device memory owned by *out (freed by et_scene_free).  Synchronous.
+ * Errors: ET_ERR_ARG (null pointers, n_tris < 0, material index out of range),
+ * ET_ERR_OOM, ET_ERR_CUDA. */
+int et_build_scene(const float* tris, const uint32_t* tri_mat, int64_t n_tris,
+                   const et_material* mats, int32_t n_mats,
+                   const et_quad_light* lights, int32_t n_lights, float env,
+                   et_scene** out, void* stream);
+void et_scene_free(et_scene* scene);
+/* Triangle count (including the lights' triangles), BVH node count and its SAH
+ * cost (C_trav = C_isect = 1, normalised by the root's surface area). */
+int et_scene_info(const et_scene* scene, int64_t* n_tris, int64_t* n_nodes, double* sah_cost);
+
+/* --------------------------------------------------------------------- render
+ * Sec. 3.2: renders frames first_frame .. first_frame + n_frames - 1 of a camera
+ * path by Monte Carlo path tracing with `spp` samples per pixel and paths of at
+ * most `max_depth` segments, next-event estimation to the quad lights with MIS,
+ * Lambertian and GGX BSDFs, and Philox4x32-10 random numbers keyed by
+ * (seed) and counted by (pixel, sample, frame, 4 * bounce + use).
+ *   cams      host [n_frames] cameras (copied; the pointer may be reused at once)
+ *   rgb       device float [n_frames][H][W][3] mean linear radiance, or NULL
+ *   logl      device float [n_frames][H][W] Eq. 1 log luminance, or NULL:
+ *             log_mode ET_LOG_EPS: ln(L + log_param); ET_LOG_PAPER: rho = log_param
+ *   records   device int32 [n_frames][H][W][spp][max_depth][2] or NULL: per path
+ *             segment the triangle hit (-1 miss, -2 not traced) and the light
+ *             sampling record (2 * light + visible, -1 none) -- for testing
+ * Calls on one scene must be issued on one stream (the scene holds the cameras).
+ * Errors: ET_ERR_ARG (W, H, spp, max_depth out of [1, 65535] / [1, 4096] / [1, 16],
+ * n_frames < 0, both outputs NULL), ET_ERR_CUDA. */
+int et_render_frames(const et_scene* scene, const et_camera* cams, int32_t n_frames,
+                     int32_t first_frame, int32_t W, int32_t H, int32_t spp,
+                     int32_t max_depth, uint64_t seed, float* rgb, float* logl,
+                     int32_t log_mode, float log_param, int32_t* records, void* stream);
+
+/* ---------------------------------------------------------- threshold events
+ * Sec. 3.1 contrast-threshold model (the method without EvSNet, the 256-SPP
+ * reference and the training target).  Per pixel, in FP64:
+ *   d = l_k - ref;  n = floor(|d| / C);  emit n events (x, y, t0 + k, sgn d);
+ *   ref += sgn(d) n C.
+ *   logl      device float [F][H][W]
+ *   ref       device double [H * W] state; when initialized == 0 the first frame
+ *             only sets ref (no events), else every frame is a step
+ *   events    device [cap];  n_events device int64 (see conventions)
+ * Errors: ET_ERR_ARG (C <= 0, sizes), ET_ERR_CUDA. */
+int et_threshold_events(const float* logl, int32_t F, int32_t H, int32_t W, float C, int32_t t0,
+                        double* ref, int32_t initialized, et_event* events, int64_t cap,
+                        int64_t* n_events, void* stream);
+
+/* --------------------------------------------------------------------- EvSNet
+ * Weights (device, FP32, packed): conv layers 0..n_layers-1 in order, each
+ * W[C][Cin][kt][ks][ks] with Cin = 1 for layer 0 and C otherwise, then the
+ * point-wise projection W[C]; biases: C per conv layer, then 1.
+ * kind ET_NET_STACK: h = ReLU(conv_i(h)) for every layer.
+ * kind ET_NET_RESIDUAL (Eq. 5): n_layers = 1 + 2M, h_0 = ReLU(conv_0(X)),
+ *   h_i = ReLU(h_{i-1} + conv_{2i}(ReLU(conv_{2i-1}(h_{i-1})))).
+ * Temporal taps are causal (tap kt-1 = current step); spatial padding is zero.
+ * BiLIF (Eq. 2-3; fire on the pre-reset potential):
+ *   V' = beta V + I;  S = +1 if V' >= vth, -1 if V' <= -vth, else 0;  V = V' - reset S.
+ * dtype: ET_F32 (CUDA cores) or ET_BF16 (tensor cores, FP32 accumulation).
+ */
+typedef struct {
+  int32_t kind, n_layers, C, kt, ks;
+  float beta, vth, reset;
+  int32_t dtype;
+  const float* w;     /* device */
+  const float* b;     /* device */
+} et_evsnet_weights;
+
+/* Per-pixel state carried between calls (all device, caller-allocated):
+ *   V       float [H * W] membrane potential
+ *   hist    float [n_layers][kt-1][C][H][W] past inputs of every layer (NULL if kt == 1)
+ *   last_l  float [H * W] log luminance of the previous frame
+ *   initialized: 0 before the first call (the first frame then only sets last_l);
+ *   et_evsnet_forward sets it to 1. */
+typedef struct {
+  float* V;
+  float* hist;
+  float* last_l;
+  int32_t H, W;
+  int32_t initialized;
+} et_evsnet_state;
+
+/* Eq. 1 (X_k = l_k - l_{k-1}) + Eq. 5-6 + BiLIF over F log frames.
+ *   logl     device float [F][H][W]
+ *   events   device [cap], n_events device int64 (see conventions); t = t0 + frame
+ *   I_out    device float [K][H][W] projection output (BiLIF input), or NULL
+ *   spikes   device int8 [K][H][W] dense spikes, or NULL
+ * K = F - 1 if the state was not initialized, else F.
+ * Errors: ET_ERR_ARG, ET_ERR_UNIMPLEMENTED (C > 32, ks > 7, kt > 9, BF16 for a
+ * shape the tensor-core kernel does not cover), ET_ERR_CUDA. */
+int et_evsnet_forward(const float* logl, int32_t F, const et_evsnet_weights* net,
+                      et_evsnet_state* state, int32_t t0, et_event* events, int64_t cap,
+                      int64_t* n_events, float* I_out, int8_t* spikes, void* stream);
+
+/* ------------------------------------------------------------------ metrics
+ * Size of a maximum matching between two event lists (host pointers): events
+ * match when they share (x, y, p) and |t_a - t_b| <= delta; each event matches
+ * at most once.  Event F1 = 2 m / (n_a + n_b).  The paper reports no event-level
+ * score; this is the project's fidelity measure of a rendered stream against the
+ * 256-SPP contrast-threshold stream.  Synchronous, host only.
+ * Errors: ET_ERR_ARG. */
+int et_event_matches(const et_event* a, int64_t n_a, const et_event* b, int64_t n_b,
+                     int32_t delta, int64_t* matches);
+
+const char* et_status_str(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EVENTTRACER_H */

@@ -171,10 +171,11 @@ class Scene:
         y0, y1 = (0, H) if rows is None else rows
         rgb = np.zeros((F, H, W, 3), np.float64)
         rec = np.full((F, H, W, spp, max_depth, 2), -3, np.int32) if records else None
-        nr = np.zeros(1, np.int64)
+        nr = np.zeros(3, np.int64)
         lib().orc_render(self._h, _p(cams), F, first_frame, W, H, y0, y1, spp, max_depth,
                          C.c_uint64(seed), _p(rgb), _p(rec), nthreads, _p(nr))
-        self.rays_traced = int(nr[0])
+        # rays traced (closest + shadow), BVH nodes visited, triangles tested
+        self.rays_traced, self.node_visits, self.tri_tests = (int(v) for v in nr)
         return (rgb, rec) if records else rgb
 
 
@@ -223,8 +224,12 @@ class ThresholdState:
 
 
 def threshold_events(logl_frames, C_thr, state: ThresholdState, t0=0):
-    """Contrast-threshold events from float32 log frames [F,H,W] -> int32 [n,4] (x,y,t,p)."""
+    """Contrast-threshold events from float32 log frames [F,H,W] -> int32 [n,4] (x,y,t,p).
+
+    The threshold C is a float32 quantity (rounded here), widened to FP64 for the
+    decision."""
     lf = _c(logl_frames, np.float32)
+    C_thr = float(np.float32(C_thr))
     F, H, W = lf.shape
     ini = C.c_int(state.initialized)
     cap = 1 << 16

@@ -55,7 +55,8 @@ void orc_occluded(const orc_scene* s, const double* o, const double* d, const do
  * (NEE record: 2*light + visible, -1 none). */
 int orc_render(const orc_scene* s, const float* cams, int F, int first_frame, int W, int H,
                int y0, int y1, int spp, int max_depth, uint64_t seed, double* rgb,
-               int32_t* records, int nthreads, int64_t* rays_traced);
+               int32_t* records, int nthreads, int64_t* work);
+/* work (optional): [3] = rays traced, BVH nodes visited, triangles tested */
 
 /* Eq. 1: luminance and log map of linear RGB.  mode 0: ln(L + eps); mode 1: the
  * paper's lin-log with threshold rho. Output is rounded to float32. */

@@ -309,10 +309,14 @@ static void closest(const orc_scene* s, const double* o, const double* d, double
   *p_out = found ? bp : -1;
 }
 
-static int occluded(const orc_scene* s, const double* o, const double* d, double tmax) {
+static int occluded_n(const orc_scene* s, const double* o, const double* d, double tmax,
+                      int64_t* nv, int64_t* nt) {
   ray_t r; ray_setup(&r, o, d);
   if (!s->use_bvh) {
-    for (int64_t i = 0; i < s->n; ++i) if (tri_hit(&r, s->tri + 9*i, tmax) > 0) return 1;
+    for (int64_t i = 0; i < s->n; ++i) {
+      if (nt) ++*nt;
+      if (tri_hit(&r, s->tri + 9*i, tmax) > 0) return 1;
+    }
     return 0;
   }
   if (s->n_nodes == 0) return 0;
@@ -320,13 +324,20 @@ static int occluded(const orc_scene* s, const double* o, const double* d, double
   while (sp) {
     const node_t* nd = &s->nodes[stack[--sp]];
     double tn;
+    if (nv) ++*nv;
     if (!box_hit(&r, nd, tmax, &tn)) continue;
     if (nd->count > 0) {
-      for (int32_t i = 0; i < nd->count; ++i)
+      for (int32_t i = 0; i < nd->count; ++i) {
+        if (nt) ++*nt;
         if (tri_hit(&r, s->tri + 9*(int64_t)s->perm[nd->first + i], tmax) > 0) return 1;
+      }
     } else { stack[sp++] = nd->left; stack[sp++] = nd->right; }
   }
   return 0;
+}
+
+static int occluded(const orc_scene* s, const double* o, const double* d, double tmax) {
+  return occluded_n(s, o, d, tmax, NULL, NULL);
 }
 
 void orc_intersect(const orc_scene* s, const double* o, const double* d, const double* tmax,
@@ -434,7 +445,7 @@ static void philox_u(uint32_t pix, uint32_t smp, uint32_t frame, uint32_t w3,
 
 static void trace_sample(const orc_scene* s, const float* cam, int W, int H, int x, int y,
                          int smp, int frame, int max_depth, const uint32_t key[2], double* Lo,
-                         int32_t* rec, int64_t* nrays) {
+                         int32_t* rec, int64_t* work) {
   uint32_t pix = (uint32_t)(y * W + x);
   double u[4];
   philox_u(pix, (uint32_t)smp, (uint32_t)frame, 0u, key, u);
@@ -448,8 +459,8 @@ static void trace_sample(const orc_scene* s, const float* cam, int W, int H, int
   double beta[3] = {1, 1, 1}, L[3] = {0, 0, 0}, prev_pdf = 0.0;
   for (int b = 1; b <= max_depth; ++b) {
     double t; int32_t prim;
-    closest(s, o, d, INFINITY, &t, &prim, NULL, NULL);
-    ++*nrays;
+    closest(s, o, d, INFINITY, &t, &prim, &work[1], &work[2]);
+    ++work[0];
     if (rec) rec[2*(b-1)] = prim;
     if (prim < 0) { for (int k = 0; k < 3; ++k) L[k] += beta[k] * s->env; break; }
     double x3[3] = {o[0] + t*d[0], o[1] + t*d[1], o[2] + t*d[2]};
@@ -492,8 +503,8 @@ static void trace_sample(const orc_scene* s, const float* cam, int W, int H, int
       double cosi = dot3(wi, ng), cosl = -dot3(wi, lt->n);
       int32_t nrec = -1;
       if (cosi > 0.0 && cosl > 0.0) {
-        int vis = !occluded(s, on, wi, dist * (1.0 - 1e-4));
-        ++*nrays;
+        int vis = !occluded_n(s, on, wi, dist * (1.0 - 1e-4), &work[1], &work[2]);
+        ++work[0];
         nrec = 2 * j + vis;
         if (vis) {
           double wil[3] = {dot3(wi, tt), dot3(wi, bt), cosi}, fc[3], pb;
@@ -520,9 +531,9 @@ static void trace_sample(const orc_scene* s, const float* cam, int W, int H, int
 
 int orc_render(const orc_scene* s, const float* cams, int F, int first_frame, int W, int H,
                int y0, int y1, int spp, int max_depth, uint64_t seed, double* rgb,
-               int32_t* records, int nthreads, int64_t* rays_traced) {
+               int32_t* records, int nthreads, int64_t* work_out) {
   uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
-  int64_t total = 0;
+  int64_t tot_r = 0, tot_v = 0, tot_t = 0;
   int64_t rows = y1 - y0;
   int64_t npix = rows * W;
 #ifdef _OPENMP
@@ -530,8 +541,8 @@ int orc_render(const orc_scene* s, const float* cams, int F, int first_frame, in
 #endif
   for (int f = 0; f < F; ++f) {
     const float* cam = cams + 13 * f;
-    int64_t cnt = 0;
-#pragma omp parallel for schedule(dynamic, 16) reduction(+:cnt)
+    int64_t cr = 0, cv = 0, ct = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(+:cr, cv, ct)
     for (int64_t q = 0; q < npix; ++q) {
       int y = y0 + (int)(q / W), x = (int)(q % W);
       double acc[3] = {0, 0, 0};
@@ -542,15 +553,17 @@ int orc_render(const orc_scene* s, const float* cams, int F, int first_frame, in
           rec = records + ((((int64_t)f * H + y) * W + x) * spp + smp) * max_depth * 2;
           for (int i = 0; i < 2 * max_depth; ++i) rec[i] = (i % 2 == 0) ? -2 : -1;
         }
-        trace_sample(s, cam, W, H, x, y, smp, first_frame + f, max_depth, key, Ls, rec, &cnt);
+        int64_t work[3] = {0, 0, 0};
+        trace_sample(s, cam, W, H, x, y, smp, first_frame + f, max_depth, key, Ls, rec, work);
+        cr += work[0]; cv += work[1]; ct += work[2];
         for (int k = 0; k < 3; ++k) acc[k] += Ls[k];
       }
       double* out = rgb + (((int64_t)f * H + y) * W + x) * 3;
       for (int k = 0; k < 3; ++k) out[k] = acc[k] / spp;
     }
-    total += cnt;
+    tot_r += cr; tot_v += cv; tot_t += ct;
   }
-  if (rays_traced) *rays_traced = total;
+  if (work_out) { work_out[0] = tot_r; work_out[1] = tot_v; work_out[2] = tot_t; }
   return 0;
 }
 

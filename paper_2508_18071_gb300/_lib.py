@@ -1,0 +1,87 @@
+"""ctypes declarations for libeventtracer (include/eventtracer.h).
+
+Argument marshalling only: every step of the hot path runs in the library's
+CUDA kernels.  Loading fails loudly when the library is missing or cannot be
+built: there is no CPU fallback.
+"""
+import ctypes as C
+import os
+
+from . import build as _build
+
+ET_OK, ET_ERR_ARG, ET_ERR_CUDA, ET_ERR_OOM, ET_ERR_CAPACITY, ET_ERR_TIMEOUT, \
+    ET_ERR_UNIMPLEMENTED = range(7)
+ET_LAMBERT, ET_GGX = 0, 1
+ET_LOG_EPS, ET_LOG_PAPER = 0, 1
+ET_F32, ET_BF16, ET_FP8 = 0, 1, 2
+ET_NET_STACK, ET_NET_RESIDUAL = 0, 1
+
+
+class et_material(C.Structure):
+    _fields_ = [("albedo", C.c_float * 3), ("roughness", C.c_float), ("type", C.c_int32)]
+
+
+class et_quad_light(C.Structure):
+    _fields_ = [("p0", C.c_float * 3), ("e1", C.c_float * 3), ("e2", C.c_float * 3),
+                ("radiance", C.c_float * 3)]
+
+
+class et_camera(C.Structure):
+    _fields_ = [("pos", C.c_float * 3), ("rot", C.c_float * 9), ("vfov_deg", C.c_float)]
+
+
+class et_evsnet_weights(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("n_layers", C.c_int32), ("C", C.c_int32),
+                ("kt", C.c_int32), ("ks", C.c_int32), ("beta", C.c_float), ("vth", C.c_float),
+                ("reset", C.c_float), ("dtype", C.c_int32), ("w", C.c_void_p), ("b", C.c_void_p)]
+
+
+class et_evsnet_state(C.Structure):
+    _fields_ = [("V", C.c_void_p), ("hist", C.c_void_p), ("last_l", C.c_void_p),
+                ("H", C.c_int32), ("W", C.c_int32), ("initialized", C.c_int32)]
+
+
+EVENT_BYTES = 12
+
+# name -> (restype, argtypes); every symbol include/eventtracer.h declares
+P, i32, i64, u64, f32, f64 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64, C.c_float, C.c_double
+SIGNATURES = {
+    "et_build_scene": (i32, [P, P, i64, P, i32, P, i32, f32, P, P]),
+    "et_scene_free": (None, [P]),
+    "et_scene_info": (i32, [P, P, P, P]),
+    "et_render_frames": (i32, [P, P, i32, i32, i32, i32, i32, i32, u64, P, P, i32, f32, P, P]),
+    "et_threshold_events": (i32, [P, i32, i32, i32, f32, i32, P, i32, P, i64, P, P]),
+    "et_evsnet_forward": (i32, [P, i32, P, P, i32, P, i64, P, P, P, P]),
+    "et_event_matches": (i32, [P, i64, P, i64, i32, P]),
+    "et_status_str": (C.c_char_p, [i32]),
+}
+
+_lib = None
+
+
+def load():
+    """Loads (building first if stale) the in-tree libeventtracer.so."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError("libeventtracer.so is missing: the CUDA library must be built")
+        L = C.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+class ETError(RuntimeError):
+    def __init__(self, fn, status):
+        msg = load().et_status_str(status).decode()
+        super().__init__("%s failed: %s (%d)" % (fn, msg, status))
+        self.status = status
+
+
+def check(fn, status):
+    if status != ET_OK:
+        raise ETError(fn, status)

@@ -1,0 +1,232 @@
+"""Python surface of libeventtracer: the same calls as include/eventtracer.h.
+
+PyTorch provides device memory and streams; these functions only marshal
+arguments into the C ABI.  All tensors passed as device buffers must be CUDA
+tensors on the current device.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+# ----------------------------------------------------------------------- scene
+class Scene:
+    """et_build_scene: geometry + BVH on the device (see inputs.py for the dict layout)."""
+
+    def __init__(self, scene: dict, stream=None):
+        lib = L.load()
+        tris = np.ascontiguousarray(scene["tris"], np.float32).reshape(-1, 9)
+        tri_mat = np.ascontiguousarray(scene["tri_mat"], np.uint32).reshape(-1)
+        mats = np.asarray(scene["materials"], np.float32).reshape(-1, 5)
+        lights = np.asarray(scene["lights"], np.float32).reshape(-1, 12)
+        cm = (L.et_material * max(len(mats), 1))()
+        for i, m in enumerate(mats):
+            cm[i].albedo[:] = [float(v) for v in m[:3]]
+            cm[i].roughness = float(m[3])
+            cm[i].type = int(m[4])
+        cl = (L.et_quad_light * max(len(lights), 1))()
+        for i, q in enumerate(lights):
+            cl[i].p0[:] = [float(v) for v in q[0:3]]
+            cl[i].e1[:] = [float(v) for v in q[3:6]]
+            cl[i].e2[:] = [float(v) for v in q[6:9]]
+            cl[i].radiance[:] = [float(v) for v in q[9:12]]
+        h = C.c_void_p()
+        st = lib.et_build_scene(tris.ctypes.data_as(C.c_void_p), tri_mat.ctypes.data_as(C.c_void_p),
+                                tris.shape[0], cm, len(mats), cl, len(lights),
+                                float(scene.get("env", 0.0)), C.byref(h), _stream(stream))
+        L.check("et_build_scene", st)
+        self._h = h
+
+    def info(self):
+        n, nn, sah = C.c_int64(), C.c_int64(), C.c_double()
+        L.check("et_scene_info", L.load().et_scene_info(self._h, C.byref(n), C.byref(nn), C.byref(sah)))
+        return {"n_tris": n.value, "n_nodes": nn.value, "sah_cost": sah.value}
+
+    def free(self):
+        if getattr(self, "_h", None):
+            L.load().et_scene_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def cameras(cams) -> C.Array:
+    cams = np.asarray(cams, np.float32).reshape(-1, 13)
+    arr = (L.et_camera * max(len(cams), 1))()
+    C.memmove(arr, np.ascontiguousarray(cams).ctypes.data, cams.nbytes)
+    return arr
+
+
+def render_frames(scene: Scene, cams, W, H, spp, max_depth, seed, first_frame=0, rgb=None,
+                  logl=None, want_rgb=True, want_logl=True, log_mode=L.ET_LOG_EPS,
+                  log_param=1e-3, records=False, stream=None):
+    """et_render_frames; returns (rgb [F,H,W,3] or None, logl [F,H,W] or None, records or None)."""
+    F = np.asarray(cams, np.float32).reshape(-1, 13).shape[0]
+    cams_c = cameras(cams)
+    dev = torch.device("cuda")
+    if want_rgb and rgb is None:
+        rgb = torch.empty((F, H, W, 3), dtype=torch.float32, device=dev)
+    if want_logl and logl is None:
+        logl = torch.empty((F, H, W), dtype=torch.float32, device=dev)
+    rec = torch.empty((F, H, W, spp, max_depth, 2), dtype=torch.int32, device=dev) if records else None
+    st = L.load().et_render_frames(scene._h, cams_c, F, first_frame, W, H, spp, max_depth,
+                                   C.c_uint64(seed), _ptr(rgb if want_rgb else None),
+                                   _ptr(logl if want_logl else None), log_mode, float(log_param),
+                                   _ptr(rec), _stream(stream))
+    L.check("et_render_frames", st)
+    return (rgb if want_rgb else None), (logl if want_logl else None), rec
+
+
+# ------------------------------------------------------------------ events
+def decode_events(raw: torch.Tensor, n: int) -> np.ndarray:
+    """Device et_event buffer (int32 [cap,3]) -> host int32 [n,4] (x, y, t, p)."""
+    w = raw[:n].cpu().numpy().astype(np.int64)
+    out = np.empty((n, 4), np.int32)
+    out[:, 0] = w[:, 0] & 0xFFFF
+    out[:, 1] = (w[:, 0] >> 16) & 0xFFFF
+    out[:, 2] = w[:, 1]
+    out[:, 3] = (w[:, 2] & 0xFF).astype(np.uint8).view(np.int8)
+    return out
+
+
+class EventBuffer:
+    """Caller-owned device event buffer and count."""
+
+    def __init__(self, cap: int):
+        self.cap = int(cap)
+        self.raw = torch.empty((max(self.cap, 1), 3), dtype=torch.int32, device="cuda")
+        self.count = torch.zeros(1, dtype=torch.int64, device="cuda")
+
+    def n(self) -> int:
+        return int(self.count.item())
+
+    def host(self) -> np.ndarray:
+        n = self.n()
+        if n > self.cap:
+            raise L.ETError("event buffer", L.ET_ERR_CAPACITY)
+        return decode_events(self.raw, n)
+
+
+def threshold_events(logl: torch.Tensor, C_thr: float, ref: torch.Tensor, initialized: bool,
+                     t0=0, buf: Optional[EventBuffer] = None, stream=None) -> EventBuffer:
+    """et_threshold_events on device log frames [F,H,W]; ref is device float64 [H*W]."""
+    F, H, W = logl.shape
+    if buf is None:
+        buf = EventBuffer(max(1 << 16, 4 * F * H * W))
+    st = L.load().et_threshold_events(_ptr(logl), F, H, W, float(C_thr), int(t0), _ptr(ref),
+                                      int(bool(initialized)), _ptr(buf.raw), buf.cap,
+                                      _ptr(buf.count), _stream(stream))
+    L.check("et_threshold_events", st)
+    return buf
+
+
+def encode_events(ev: np.ndarray) -> np.ndarray:
+    """host int32 [n,4] (x, y, t, p) -> packed et_event records (int32 [n,3])."""
+    ev = np.asarray(ev, np.int64).reshape(-1, 4)
+    out = np.empty((len(ev), 3), np.uint32)
+    out[:, 0] = (ev[:, 0] & 0xFFFF) | ((ev[:, 1] & 0xFFFF) << 16)
+    out[:, 1] = ev[:, 2]
+    out[:, 2] = ev[:, 3].astype(np.int8).view(np.uint8)
+    return out.view(np.int32)
+
+
+def event_f1(pred: np.ndarray, ref: np.ndarray, delta: int) -> float:
+    """Event F1 of two host event lists [n,4] via et_event_matches; both empty -> 1."""
+    na, nb = len(pred), len(ref)
+    if na == 0 and nb == 0:
+        return 1.0
+    a = np.ascontiguousarray(encode_events(pred))
+    b = np.ascontiguousarray(encode_events(ref))
+    m = C.c_int64()
+    st = L.load().et_event_matches(a.ctypes.data_as(C.c_void_p), na, b.ctypes.data_as(C.c_void_p),
+                                   nb, int(delta), C.byref(m))
+    L.check("et_event_matches", st)
+    return 2.0 * m.value / (na + nb)
+
+
+# ------------------------------------------------------------------ EvSNet
+@dataclass
+class EvsNetDev:
+    kind: int
+    n_layers: int
+    C: int
+    kt: int
+    ks: int
+    beta: float
+    vth: float
+    reset: float
+    w: torch.Tensor
+    b: torch.Tensor
+    dtype: int = L.ET_F32
+
+    @staticmethod
+    def from_dict(d: dict, dtype=L.ET_F32):
+        return EvsNetDev(d["kind"], d["n_layers"], d["C"], d["kt"], d["ks"], float(d["beta"]),
+                         float(d["vth"]), float(d["reset"]),
+                         torch.as_tensor(np.asarray(d["w"], np.float32)).cuda().contiguous(),
+                         torch.as_tensor(np.asarray(d["b"], np.float32)).cuda().contiguous(), dtype)
+
+    def c_struct(self):
+        return L.et_evsnet_weights(self.kind, self.n_layers, self.C, self.kt, self.ks, self.beta,
+                                   self.vth, self.reset, self.dtype, self.w.data_ptr(),
+                                   self.b.data_ptr())
+
+
+class EvsStateDev:
+    """et_evsnet_state: device V, history and last log frame."""
+
+    def __init__(self, net: EvsNetDev, H, W, V0: Optional[torch.Tensor] = None):
+        self.H, self.W = H, W
+        self.V = torch.zeros(H * W, dtype=torch.float32, device="cuda") if V0 is None \
+            else V0.reshape(-1).float().cuda().clone()
+        nh = net.n_layers * max(net.kt - 1, 0) * net.C * H * W
+        self.hist = torch.zeros(max(nh, 1), dtype=torch.float32, device="cuda")
+        self.last_l = torch.zeros(H * W, dtype=torch.float32, device="cuda")
+        self.initialized = 0
+        self._has_hist = net.kt > 1
+
+    def c_struct(self):
+        return L.et_evsnet_state(self.V.data_ptr(), self.hist.data_ptr() if self._has_hist else None,
+                                 self.last_l.data_ptr(), self.H, self.W, self.initialized)
+
+
+def evsnet_forward(logl: torch.Tensor, net: EvsNetDev, state: EvsStateDev, t0=0,
+                   buf: Optional[EventBuffer] = None, want_I=False, want_spikes=False, stream=None):
+    """et_evsnet_forward; returns (EventBuffer, I [K,H,W] or None, spikes [K,H,W] or None)."""
+    F, H, W = logl.shape
+    K = F - (0 if state.initialized else 1)
+    if buf is None:
+        buf = EventBuffer(max(1 << 16, max(K, 1) * H * W))
+    I = torch.empty((max(K, 1), H, W), dtype=torch.float32, device="cuda") if want_I else None
+    S = torch.empty((max(K, 1), H, W), dtype=torch.int8, device="cuda") if want_spikes else None
+    cw = net.c_struct()
+    cs = state.c_struct()
+    st = L.load().et_evsnet_forward(_ptr(logl), F, C.byref(cw), C.byref(cs), int(t0), _ptr(buf.raw),
+                                    buf.cap, _ptr(buf.count), _ptr(I), _ptr(S), _stream(stream))
+    L.check("et_evsnet_forward", st)
+    state.initialized = cs.initialized
+    return buf, (I[:K] if I is not None else None), (S[:K] if S is not None else None)

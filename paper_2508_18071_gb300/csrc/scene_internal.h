@@ -1,0 +1,15 @@
+// Host-side definition of the opaque et_scene handle.
+#pragma once
+#include "et_internal.cuh"
+
+struct et_scene {
+  float4* d_tris = nullptr;
+  BvhNode* d_nodes = nullptr;
+  DevMaterial* d_mats = nullptr;
+  DevLight* d_lights = nullptr;
+  et_camera* d_cams = nullptr;   // camera staging for et_render_frames
+  int64_t cam_cap = 0;
+  int64_t n_tris = 0, n_nodes = 0;
+  double sah = 0.0;
+  et_scene_dev dev{};
+};

@@ -1,0 +1,185 @@
+"""Parity of the event kernels with the oracle.
+
+Threshold generator: identical float32 log frames in, bit-exact event multisets
+and FP64 reference state out (the decision is FP64 with explicit rounding on
+both sides).  EvSNet FP32: projection output I within 1e-5 (1 + |I|), membrane
+state within 1e-5 (1 + |V|), and identical events on every pixel whose oracle
+membrane potential never came within 1e-4 of +-Vth (elsewhere the FP32 kernel
+and the FP64 oracle may legitimately decide differently)."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2508_18071_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    assert torch.cuda.is_available()
+    from paper_2508_18071_gb300 import api as A
+    return A
+
+
+def _sorted(ev):
+    import oracle
+    return oracle.sort_events(ev)
+
+
+# ---------------------------------------------------------------- threshold
+@pytest.mark.parametrize("F,H,W", [(20, 64, 64), (9, 23, 37), (2, 1, 1), (1, 5, 5)])
+def test_threshold_exact(api, orc, F, H, W):
+    lf = inputs.random_logl_clip(1, F, H, W)
+    C = 0.2
+    st = orc.ThresholdState.new(H, W)
+    ref_ev = orc.threshold_events(lf, C, st)
+    d = torch.as_tensor(lf).cuda()
+    ref = torch.zeros(H * W, dtype=torch.float64, device="cuda")
+    buf = api.threshold_events(d, C, ref, False)
+    ev = buf.host()
+    assert np.array_equal(_sorted(ev), _sorted(ref_ev))
+    np.testing.assert_array_equal(ref.cpu().numpy(), st.ref)
+
+
+def test_threshold_streaming_and_capacity(api, orc):
+    F, H, W = 30, 40, 50
+    lf = inputs.random_logl_clip(2, F, H, W, jump_p=0.05)
+    st = orc.ThresholdState.new(H, W)
+    ref_ev = orc.threshold_events(lf, 0.15, st)
+    d = torch.as_tensor(lf).cuda()
+    ref = torch.zeros(H * W, dtype=torch.float64, device="cuda")
+    parts = []
+    for i, (a, b) in enumerate([(0, 1), (1, 12), (12, 30)]):
+        buf = api.threshold_events(d[a:b].contiguous(), 0.15, ref, i > 0, t0=a)
+        parts.append(buf.host())
+    assert np.array_equal(_sorted(np.concatenate(parts)), _sorted(ref_ev))
+    # a too-small buffer keeps the first cap events and reports the full count
+    ref2 = torch.zeros(H * W, dtype=torch.float64, device="cuda")
+    small = api.EventBuffer(100)
+    api.threshold_events(d, 0.15, ref2, False, buf=small)
+    assert small.n() == len(ref_ev) > 100
+    with pytest.raises(Exception):
+        small.host()
+
+
+def test_threshold_full_size(api, orc):
+    """1280 x 720 x 12 frames, every event compared."""
+    F, H, W = 12, 720, 1280
+    lf = inputs.random_logl_clip(5, F, H, W)
+    st = orc.ThresholdState.new(H, W)
+    ref_ev = orc.threshold_events(lf, 0.2, st)
+    d = torch.as_tensor(lf).cuda()
+    ref = torch.zeros(H * W, dtype=torch.float64, device="cuda")
+    ev = api.threshold_events(d, 0.2, ref, False).host()
+    assert len(ev) == len(ref_ev) > 100000
+    assert np.array_equal(_sorted(ev), _sorted(ref_ev))
+
+
+# ------------------------------------------------------------------ EvSNet
+def _net(orc, d):
+    return orc.EvsNet(d["kind"], d["n_layers"], d["C"], d["kt"], d["ks"], d["beta"], d["vth"],
+                      d["reset"], np.asarray(d["w"], np.float64), np.asarray(d["b"], np.float64))
+
+
+def _check_evsnet(api, orc, d, lf, chunks=None, margin_tol=1e-4, max_tie_frac=0.01):
+    F, H, W = lf.shape
+    onet = _net(orc, d)
+    ost = orc.EvsState.new(onet, H, W)
+    oev, oI, mg = orc.evsnet_forward(lf, onet, ost, want_I=True, want_margin=True)
+    gnet = api.EvsNetDev.from_dict(d)
+    gst = api.EvsStateDev(gnet, H, W)
+    dl = torch.as_tensor(lf).cuda()
+    evs, Is = [], []
+    for a, b in (chunks or [(0, F)]):
+        buf, I, _ = api.evsnet_forward(dl[a:b].contiguous(), gnet, gst, t0=a, want_I=True)
+        evs.append(buf.host())
+        if I is not None and I.shape[0] == (b - a - (1 if a == 0 else 0)):
+            Is.append(I.cpu().numpy())
+    ev = np.concatenate(evs)
+    gI = np.concatenate(Is)
+    clean = mg > margin_tol                       # pixels with no near-threshold decision
+    assert 1.0 - clean.mean() <= max_tie_frac
+    cI = clean[None].repeat(gI.shape[0], 0)
+    np.testing.assert_array_less(np.abs(gI - oI)[cI], 1e-5 * (1 + np.abs(oI[cI])))
+    V = gst.V.cpu().numpy().reshape(H, W)
+    np.testing.assert_array_less(np.abs(V - ost.V.reshape(H, W))[clean],
+                                 1e-5 * (1 + np.abs(ost.V.reshape(H, W)[clean])))
+    keep = lambda e: e[clean[e[:, 1], e[:, 0]]]
+    assert np.array_equal(_sorted(keep(ev)), _sorted(keep(oev)))
+    return ev, oev
+
+
+def test_evsnet_tiny_config(api, orc):
+    """Two 3x3 conv layers, 8 channels, weights N(0, 0.1), 8 frames of 64 x 64."""
+    d = inputs.random_evsnet(0, 2, 8, 1, 3, seed=2, vth=0.05, beta=1.0)
+    lf = inputs.random_logl_clip(3, 8, 64, 64, step_std=0.3)
+    ev, oev = _check_evsnet(api, orc, d, lf)
+    assert len(oev) > 100
+
+
+def test_evsnet_four_layer_16ch_ragged(api, orc):
+    """Four 3x3 layers, 16 channels, thresholds +-0.5, leak 0.9, ragged 45 x 37."""
+    d = inputs.random_evsnet(0, 4, 16, 1, 3, seed=12, vth=0.5, beta=0.9)
+    lf = inputs.random_logl_clip(4, 20, 37, 45, step_std=0.4)
+    ev, oev = _check_evsnet(api, orc, d, lf)
+    assert len(oev) > 100
+
+
+def test_evsnet_paper_form_kernel7_residual(api, orc):
+    """Eq. 5 form: temporal kernel 7, M = 3 residual blocks, 16 channels,
+    streamed in three chunks (the history crosses chunk boundaries)."""
+    d = inputs.random_evsnet(1, 7, 16, 7, 1, seed=5, vth=0.3, beta=0.95)
+    lf = inputs.random_logl_clip(6, 30, 19, 21, step_std=0.3)
+    ev, oev = _check_evsnet(api, orc, d, lf, chunks=[(0, 5), (5, 6), (6, 30)])
+    assert len(oev) > 50
+
+
+def test_identity_evsnet_equals_gpu_threshold(api, orc):
+    """P6: the hand-set identity network with beta = 1, Vth = reset = C reproduces
+    the threshold generator while steps stay below C."""
+    C = 0.2
+    rng = np.random.default_rng(4)
+    F, H, W = 40, 33, 35
+    steps = rng.uniform(-0.19, 0.19, (F, H, W))
+    steps[0] = 0
+    lf = (rng.normal(0, 1, (H, W)) + np.cumsum(steps, 0)).astype(np.float32)
+    dl = torch.as_tensor(lf).cuda()
+    ref = torch.zeros(H * W, dtype=torch.float64, device="cuda")
+    thr = api.threshold_events(dl, C, ref, False).host()
+    d = inputs.identity_evsnet(0, 2, 2, 1, 3, vth=C)
+    onet = _net(orc, d)
+    _, _, mg = orc.evsnet_forward(lf, onet, orc.EvsState.new(onet, H, W), want_margin=True)
+    gnet = api.EvsNetDev.from_dict(d)
+    ev = api.evsnet_forward(dl, gnet, api.EvsStateDev(gnet, H, W))[0].host()
+    clean = mg > 1e-5
+    keep = lambda e: e[clean[e[:, 1], e[:, 0]]]
+    assert clean.mean() > 0.99
+    assert np.array_equal(_sorted(keep(ev)), _sorted(keep(thr)))
+
+
+def test_evsnet_streaming_bitwise(api):
+    d = inputs.random_evsnet(0, 4, 16, 1, 3, seed=1, vth=0.5, beta=0.9)
+    lf = torch.as_tensor(inputs.random_logl_clip(7, 25, 40, 40, step_std=0.4)).cuda()
+    net = api.EvsNetDev.from_dict(d)
+    st = api.EvsStateDev(net, 40, 40)
+    _, I, S = api.evsnet_forward(lf, net, st, want_I=True, want_spikes=True)
+    st2 = api.EvsStateDev(net, 40, 40)
+    I2, S2 = [], []
+    for a, b in [(0, 3), (3, 4), (4, 25)]:
+        _, i, s = api.evsnet_forward(lf[a:b].contiguous(), net, st2, t0=a, want_I=True,
+                                     want_spikes=True)
+        I2.append(i)
+        S2.append(s)
+    assert torch.equal(torch.cat(I2), I) and torch.equal(torch.cat(S2), S)
+    assert torch.equal(st.V, st2.V)
+
+
+def test_evsnet_rejects_unsupported(api):
+    from paper_2508_18071_gb300 import _lib
+    d = inputs.random_evsnet(1, 3, 4, 3, 3, seed=1)
+    net = api.EvsNetDev.from_dict(d)
+    lf = torch.zeros((3, 8, 8), device="cuda")
+    with pytest.raises(_lib.ETError) as e:
+        api.evsnet_forward(lf, net, api.EvsStateDev(net, 8, 8))
+    assert e.value.status == _lib.ET_ERR_UNIMPLEMENTED

@@ -70,7 +70,7 @@ def test_threshold_jump_emits_floor_count(orc):
 
 def test_threshold_invariants_and_streaming(orc):
     lf = inputs.random_logl_clip(3, 40, 8, 9)
-    C = 0.2
+    C = float(np.float32(0.2))                     # the threshold is a float32 quantity
     st = orc.ThresholdState.new(8, 9)
     ev = orc.threshold_events(lf, C, st)
     # telescoping: ref = l_0 + C * (sum of polarities); |l_last - ref| < C
