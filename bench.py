@@ -46,7 +46,10 @@ def parse():
     p.add_argument("--baseline-frames", type=int, default=12)
     p.add_argument("--no-baseline", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
-    p.add_argument("--cpu-rows", type=int, default=96, help="oracle sample: rows of one frame")
+    p.add_argument("--cpu-rows", type=int, default=720, help="oracle sample: rows per frame")
+    p.add_argument("--cpu-frames", type=int, default=2, help="oracle sample: frames")
+    p.add_argument("--width", type=int, default=1280, help="smaller sizes: profiling cases only")
+    p.add_argument("--height", type=int, default=720)
     return p.parse_args()
 
 
@@ -123,17 +126,13 @@ def cpu_baseline(scene, net_d, spp, rows, frames_for_render=1):
     t0 = time.perf_counter()
     o = oracle.Scene(scene["tris"], scene["tri_mat"], scene["materials"], scene["lights"], scene["env"])
     t_bvh = time.perf_counter() - t0
-    cams = inputs.city_path(1, first=500)
-    step = max(1, H_ // rows)
-    ys = list(range(0, H_, step))[:rows]
-    t_r = 0.0
-    work = np.zeros(3)
-    for y in ys:
-        t0 = time.perf_counter()
-        o.render(cams, W_, H_, spp, DEPTH, SEED, first_frame=500, rows=(y, y + 1), nthreads=cores)
-        t_r += time.perf_counter() - t0
-        work += [o.rays_traced, o.node_visits, o.tri_tests]
-    t_frame_render = t_r * H_ / len(ys)
+    cams = inputs.city_path(frames_for_render, first=500)
+    t0 = time.perf_counter()
+    o.render(cams, W_, H_, spp, DEPTH, SEED, first_frame=500, rows=(0, rows), nthreads=cores)
+    t_r = time.perf_counter() - t0
+    work = np.array([o.rays_traced, o.node_visits, o.tri_tests], float)
+    ys = range(rows)
+    t_frame_render = t_r * H_ / rows / frames_for_render
     # EvSNet on a 128x128 crop for 8 steps, extrapolated per 720p frame
     onet = oracle.EvsNet(net_d["kind"], net_d["n_layers"], net_d["C"], net_d["kt"], net_d["ks"],
                          net_d["beta"], net_d["vth"], net_d["reset"],
@@ -145,12 +144,12 @@ def cpu_baseline(scene, net_d, spp, rows, frames_for_render=1):
     t_e = time.perf_counter() - t0
     t_frame_evs = t_e / 8 * (W_ * H_) / (128 * 128)
     sec_per_video_s = 1000.0 * (t_frame_render + t_frame_evs)
-    samples = len(ys) * W_ * spp
+    samples = len(ys) * W_ * spp * frames_for_render
     return {
         "value": 60.0 / sec_per_video_s, "unit": UNIT, "cores": cores, "kind": "oracle",
-        "sample": "%d rows x 1280 px x %d spp of one frame rendered (%.1f s) + EvSNet on 128x128 x 8 "
-                  "steps (%.1f s), extrapolated to 1000 frames of 1280x720; BVH build %.1f s excluded"
-                  % (len(ys), spp, t_r, t_e, t_bvh),
+        "sample": "%d frame(s) x %d rows x 1280 px x %d spp rendered (%.1f s) + EvSNet on 128x128 "
+                  "x 8 steps (%.1f s), extrapolated to 1000 frames of 1280x720; BVH build %.1f s "
+                  "excluded" % (frames_for_render, len(ys), spp, t_r, t_e, t_bvh),
         "_work": {"rays_per_sample": work[0] / samples,
                   "flops_per_ray": (24.0 * work[1] + 40.0 * work[2]) / max(work[0], 1),
                   "bytes_per_ray": (64.0 * work[1] + 36.0 * work[2]) / max(work[0], 1)},
@@ -218,7 +217,9 @@ def load_net_host():
 
 
 def main():
+    global W_, H_
     args = parse()
+    W_, H_ = args.width, args.height
     if args.impl == "reference":
         run_reference(args)
         return
@@ -327,10 +328,10 @@ def main():
         "dtype": "f32 render + %s EvSNet" % ("f32" if dtype == _lib.ET_F32 else "bf16"),
         "data": "synthetic (procedural city block, random-init EvSNet)" if not net_d.get("trained")
                 else "synthetic (procedural city block, EvSNet trained on procedural clips)",
-        "config": {"workload": "city block %d tris (BVH %d nodes), 1280x720, 1 kHz, %d spp, depth 5, "
+        "config": {"workload": "city block %d tris (BVH %d nodes), %dx%d, 1 kHz, %d spp, depth 5, "
                                "EvSNet %d x conv%dx%d C%d + BiLIF" % (info["n_tris"], info["n_nodes"],
-                                                                       args.spp, net.n_layers, net.ks,
-                                                                       net.ks, net.C),
+                                                                       W_, H_, args.spp, net.n_layers,
+                                                                       net.ks, net.ks, net.C),
                    "frames_per_step": F, "l2": "flushed between steps (256 MB write)",
                    "parallelism": "replicas: each rank renders its own path segment"},
         "wall_s_timed": wall,
@@ -348,7 +349,7 @@ def main():
     # ---- CPU oracle on a bounded sample (also yields the algorithmic work per ray)
     cpu = None
     if not args.no_cpu:
-        cpu = cpu_baseline(scene, net_d, args.spp, args.cpu_rows)
+        cpu = cpu_baseline(scene, net_d, args.spp, min(args.cpu_rows, H_), args.cpu_frames)
         work = cpu.pop("_work")
         line["cpu_baseline"] = cpu
         flops_launch = work["flops_per_ray"] * work["rays_per_sample"] * npix * args.spp * F

@@ -132,15 +132,32 @@ class EventBuffer:
 
 
 def threshold_events(logl: torch.Tensor, C_thr: float, ref: torch.Tensor, initialized: bool,
-                     t0=0, buf: Optional[EventBuffer] = None, stream=None) -> EventBuffer:
-    """et_threshold_events on device log frames [F,H,W]; ref is device float64 [H*W]."""
+                     t0=0, buf: Optional[EventBuffer] = None, stream=None,
+                     grow: bool = True) -> EventBuffer:
+    """et_threshold_events on device log frames [F,H,W]; ref is device float64 [H*W].
+
+    With grow=True and no caller buffer, an overflowing call is repeated once
+    with a buffer of the reported size (the state is restored first); this
+    synchronises the stream."""
     F, H, W = logl.shape
-    if buf is None:
+    own = buf is None
+    if own:
         buf = EventBuffer(max(1 << 16, 4 * F * H * W))
-    st = L.load().et_threshold_events(_ptr(logl), F, H, W, float(C_thr), int(t0), _ptr(ref),
-                                      int(bool(initialized)), _ptr(buf.raw), buf.cap,
-                                      _ptr(buf.count), _stream(stream))
-    L.check("et_threshold_events", st)
+    saved = ref.clone() if (own and grow) else None
+
+    def call(b):
+        st = L.load().et_threshold_events(_ptr(logl), F, H, W, float(C_thr), int(t0), _ptr(ref),
+                                          int(bool(initialized)), _ptr(b.raw), b.cap,
+                                          _ptr(b.count), _stream(stream))
+        L.check("et_threshold_events", st)
+
+    call(buf)
+    if saved is not None:
+        n = buf.n()
+        if n > buf.cap:
+            ref.copy_(saved)
+            buf = EventBuffer(n)
+            call(buf)
     return buf
 
 

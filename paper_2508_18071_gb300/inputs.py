@@ -196,10 +196,10 @@ def random_scene_clip_path(seed, n_frames=65, cube=10.0):
     return np.stack(out)
 
 
-def city_block(seed=21, n_boxes=41667, street_half=6.0, lot=9.0):
-    """~500k triangles: n_boxes closed boxes (12 triangles each) on a street grid
-    along -z, building heights log-normal; a ground quad; four 1 m x 1 m street
-    lights of radiance 50 at 8 m; environment 0.1."""
+def city_block(seed=21, n_boxes=40000, street_half=6.0, lot=9.0):
+    """~500k triangles: n_boxes closed boxes (12 triangles each, 480k) on a street
+    grid along -z, building heights log-normal; a 4 km ground in 40 m tiles (20k);
+    four 1 m x 1 m street lights of radiance 50 at 8 m; environment 0.1."""
     rng = np.random.default_rng(seed)
     mats = [[0.5, 0.5, 0.5, 0.5, 0]]                                  # ground
     for _ in range(64):
@@ -234,8 +234,16 @@ def city_block(seed=21, n_boxes=41667, street_half=6.0, lot=9.0):
         s = rng.uniform(0.3, 2.0, 3) * np.array([1.0, 0.8, 1.0])
         groups.append((_box((x - s[0] / 2, 0, z - s[2] / 2), (x + s[0] / 2, s[1], z + s[2] / 2),
                             rot_y=rng.uniform(0, math.pi)), 1 + int(rng.integers(64))))
-    L = 2000.0
-    groups.append((_quad((-L, 0, L), (0, 0, -2 * L), (2 * L, 0, 0)), 0))
+    # ground: 4 km x 4 km in 40 m tiles (100 x 100 quads); kilometre-sized
+    # triangles would put FP32 hit points ~1e-4 m off near the camera
+    L, tile = 2000.0, 40.0
+    n = int(2 * L / tile)
+    ground = []
+    for i in range(n):
+        for j in range(n):
+            x0, z0 = -L + tile * i, L - tile * j
+            ground.extend(_quad((x0, 0, z0), (0, 0, -tile), (tile, 0, 0)))
+    groups.append((ground, 0))
     lights = [[-0.5, 8.0, -5.0 - 10.0 * i - 0.5, 1.0, 0, 0, 0, 0, 1.0, 50, 45, 40]
               for i in range(4)]
     return _pack(groups, mats, lights, env=0.1)

