@@ -11,8 +11,10 @@ Conditioning: a shading point a hair below a light's plane sees the light at
 grazing incidence, and cos(theta_l) = (p_l - x) . n_l is then computed from a
 hit point whose FP32 position error (~1e-7 m) is a sizeable fraction of the
 1e-4 m height difference: such pixels differ by up to ~5e-3 relative but by
-under 1e-6 absolute (their radiance is ~1e-4).  So every agreeing pixel must be
-within 1e-4 |ref| + 1e-6, and at least 99.9 % of them within the strict
+under 1e-6 absolute (their radiance is ~1e-4).  A glossy GGX lobe of roughness
+alpha = 0.05 amplifies direction rounding by d ln D / d theta ~ 4 / alpha^2
+~ 1600, i.e. 6e-8 -> 1e-4 relative per glossy bounce.  So every agreeing pixel
+must be within 2e-3 |ref| + 1e-6, and at least 99.9 % of them within the strict
 1e-4 |ref| + 1e-7."""
 import math
 
@@ -26,11 +28,12 @@ pytestmark = pytest.mark.gpu
 
 RTOL, ATOL = 1e-4, 1e-7
 ATOL_GRAZING = 1e-6
+RTOL_ILL = 2e-3
 STRICT_FRAC = 0.999
 
 
 def _check_radiance(rgb, orgb, agree):
-    loose = rel_close(rgb, orgb, RTOL, ATOL_GRAZING).all(-1)
+    loose = rel_close(rgb, orgb, RTOL_ILL, ATOL_GRAZING).all(-1)
     strict = rel_close(rgb, orgb, RTOL, ATOL).all(-1)
     bad = np.argwhere(agree & ~loose)
     assert len(bad) == 0, [(tuple(i), rgb[tuple(i)].tolist(), orgb[tuple(i)].tolist())
