@@ -121,8 +121,15 @@ class EventBuffer:
         self.raw = torch.empty((max(self.cap, 1), 3), dtype=torch.int32, device="cuda")
         self.count = torch.zeros(1, dtype=torch.int64, device="cuda")
 
+    TIMEOUT_BIT = 1 << 62
+
     def n(self) -> int:
-        return int(self.count.item())
+        """Event count; raises if a kernel's bounded device-side wait gave up
+        (the kernels signal that by setting bit 62 of the count)."""
+        v = int(self.count.item())
+        if v >= self.TIMEOUT_BIT:
+            raise L.ETError("device-side wait", L.ET_ERR_TIMEOUT)
+        return v
 
     def host(self) -> np.ndarray:
         n = self.n()

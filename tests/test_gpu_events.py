@@ -186,3 +186,110 @@ def test_evsnet_rejects_unsupported(api):
     with pytest.raises(_lib.ETError) as e:
         api.evsnet_forward(lf, net, api.EvsStateDev(net, 8, 8))
     assert e.value.status == _lib.ET_ERR_UNIMPLEMENTED
+
+
+# ------------------------------------------------------------- EvSNet BF16
+def _dyadic_net(seed, L=4, C=16, density=0.1):
+    """Weights in {-1/2, 0, +1/2} (10 % non-zero), projection +-1, zero biases:
+    with inputs that are multiples of 1/4, every activation stays a short dyadic
+    fraction (checked to be exactly representable in BF16 for these shapes), so
+    every BF16 rounding in the tensor-core path is exact and its result must equal
+    the FP32 path bit for bit."""
+    rng = np.random.default_rng(seed)
+    d = inputs.random_evsnet(0, L, C, 1, 3, seed=seed, vth=0.5, beta=1.0)
+    w = rng.choice([-0.5, 0.0, 0.5], size=d["w"].shape, p=[density / 2, 1 - density, density / 2])
+    nproj = C
+    w[-nproj:] = rng.choice([-1.0, 1.0], size=nproj)
+    d["w"] = w.astype(np.float32)
+    d["b"] = np.zeros_like(d["b"])
+    return d
+
+
+def _dyadic_clip(seed, F, H, W):
+    rng = np.random.default_rng(seed)
+    steps = rng.integers(-2, 3, (F, H, W)) / 4.0
+    steps[0] = 0
+    return (np.cumsum(steps, 0)).astype(np.float32)
+
+
+def _run(api, d, lf, dtype, chunks=None):
+    F, H, W = lf.shape
+    net = api.EvsNetDev.from_dict(d, dtype)
+    st = api.EvsStateDev(net, H, W)
+    dl = torch.as_tensor(lf).cuda()
+    evs, Is, Ss = [], [], []
+    for a, b in (chunks or [(0, F)]):
+        buf, I, S = api.evsnet_forward(dl[a:b].contiguous(), net, st, t0=a, want_I=True,
+                                       want_spikes=True)
+        evs.append(buf.host())
+        if I is not None and I.shape[0] == (b - a - (1 if a == 0 else 0)):
+            Is.append(I.cpu().numpy())
+            Ss.append(S.cpu().numpy())
+    return np.concatenate(evs), np.concatenate(Is), np.concatenate(Ss), st.V.cpu().numpy()
+
+
+@pytest.mark.parametrize("H,W,L,C", [(64, 96, 4, 16), (37, 45, 4, 16), (40, 70, 3, 32), (20, 33, 2, 8)])
+def test_evsnet_bf16_exact_on_dyadic_data(api, H, W, L, C):
+    from paper_2508_18071_gb300 import _lib
+    d = _dyadic_net(3, L=L, C=C)
+    lf = _dyadic_clip(4, 9, H, W)
+    ev32, I32, S32, V32 = _run(api, d, lf, _lib.ET_F32)
+    ev16, I16, S16, V16 = _run(api, d, lf, _lib.ET_BF16)
+    assert np.abs(I32).max() > 0.1
+    np.testing.assert_array_equal(I16, I32)
+    np.testing.assert_array_equal(S16, S32)
+    np.testing.assert_array_equal(V16, V32)
+    assert np.array_equal(_sorted(ev16), _sorted(ev32))
+
+
+def test_evsnet_bf16_random_weights_vs_oracle_and_fp32(api, orc):
+    """Random N(0, 0.1) weights, 4 layers, 16 channels: I within the BF16 error
+    envelope of the FP64 oracle, and event F1 >= 0.95 against the FP32 path."""
+    from paper_2508_18071_gb300 import _lib
+    d = inputs.random_evsnet(0, 4, 16, 1, 3, seed=12, vth=0.1, beta=0.9)
+    lf = inputs.random_logl_clip(4, 16, 80, 112, step_std=0.4)
+    ev32, I32, _, _ = _run(api, d, lf, _lib.ET_F32)
+    ev16, I16, _, _ = _run(api, d, lf, _lib.ET_BF16)
+    onet = _net(orc, d)
+    _, oI, _ = orc.evsnet_forward(lf, onet, orc.EvsState.new(onet, 80, 112), want_I=True)
+    scale = np.abs(oI).mean()
+    # three BF16 roundings of activations and one of the weights: ~4 x 2^-9 relative
+    assert np.all(np.abs(I16 - oI) <= 2e-2 * (np.abs(oI) + scale))
+    assert np.abs(I16 - oI).mean() <= 5e-3 * scale
+    assert len(ev32) > 1000
+    assert api.event_f1(ev16, ev32, 0) >= 0.95
+
+
+def test_evsnet_bf16_streaming_bitwise(api):
+    from paper_2508_18071_gb300 import _lib
+    d = inputs.random_evsnet(0, 4, 16, 1, 3, seed=1, vth=0.1, beta=0.9)
+    lf = inputs.random_logl_clip(7, 25, 40, 72, step_std=0.4)
+    ev, I, S, V = _run(api, d, lf, _lib.ET_BF16)
+    ev2, I2, S2, V2 = _run(api, d, lf, _lib.ET_BF16, chunks=[(0, 3), (3, 4), (4, 25)])
+    np.testing.assert_array_equal(I2, I)
+    np.testing.assert_array_equal(S2, S)
+    np.testing.assert_array_equal(V2, V)
+
+
+def test_evsnet_bf16_full_size(api, orc):
+    """1280 x 720, 6 frames, the benchmark's network shape: sampled pixels against
+    the oracle (a 64 x 64 crop at the image corner and one in the middle), and
+    event F1 >= 0.95 against the FP32 path on the full frame."""
+    from paper_2508_18071_gb300 import _lib
+    d = inputs.random_evsnet(0, 4, 16, 1, 3, seed=12, vth=0.1, beta=0.9)
+    lf = inputs.random_logl_clip(9, 6, 720, 1280, step_std=0.4)
+    ev32, I32, _, _ = _run(api, d, lf, _lib.ET_F32)
+    ev16, I16, _, _ = _run(api, d, lf, _lib.ET_BF16)
+    assert api.event_f1(ev16, ev32, 0) >= 0.95
+    onet = _net(orc, d)
+    for (y0, x0) in [(0, 0), (300, 600), (656, 1216)]:
+        # the oracle on a crop with a 4-pixel margin reproduces the interior exactly
+        ya, xa = max(0, y0 - 4), max(0, x0 - 4)
+        yb, xb = min(720, y0 + 68), min(1280, x0 + 68)
+        crop = lf[:, ya:yb, xa:xb]
+        _, oI, _ = orc.evsnet_forward(crop, onet, orc.EvsState.new(onet, yb - ya, xb - xa), want_I=True)
+        iy, ix = y0 - ya, x0 - xa
+        o = oI[:, iy:iy + 64, ix:ix + 64]
+        g = I16[:, y0:y0 + 64, x0:x0 + 64]
+        scale = np.abs(o).mean()
+        assert np.all(np.abs(g - o) <= 2e-2 * (np.abs(o) + scale))
