@@ -48,6 +48,7 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-rows", type=int, default=720, help="oracle sample: rows per frame")
     p.add_argument("--cpu-frames", type=int, default=2, help="oracle sample: frames")
+    p.add_argument("--evsnet-dtype", default="bf16", choices=["f32", "bf16"])
     p.add_argument("--width", type=int, default=1280, help="smaller sizes: profiling cases only")
     p.add_argument("--height", type=int, default=720)
     return p.parse_args()
@@ -240,7 +241,7 @@ def main():
     scene = inputs.city_block(seed=21)
     g = api.Scene(scene)
     info = g.info()
-    dtype = _lib.ET_F32
+    dtype = _lib.ET_BF16 if args.evsnet_dtype == "bf16" else _lib.ET_F32
     net, net_d = load_net(dtype)
     F = args.frames
     npix = W_ * H_
@@ -343,6 +344,25 @@ def main():
         "evsnet_ms_per_frame": statistics.mean(t_evs) / F,
         "clocks": clk.summary(local),
     }
+    # EvSNet kernel: algorithmic MACs per pixel-step of the conv stack + projection
+    C, Lr = net.C, net.n_layers
+    macs = 9 * C + (Lr - 1) * 9 * C * C + C
+    flops_evs = 2.0 * macs * npix * F
+    t_evs_s = statistics.mean(t_evs) / 1e3
+    peaks = {}
+    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk_path):
+        peaks = json.load(open(pk_path))
+    if dtype == _lib.ET_BF16:
+        pk = peaks.get("bf16_tflops_sustained") or 1700.0
+        src = "MEASURED_PEAKS bf16_tflops_sustained (of measured)" if "bf16_tflops_sustained" in peaks \
+            else "fallback 1.7 PFLOP/s sustained"
+        line["roofline_evsnet"] = {"bound": "tensor", "kernel": "evsnet_tc_kernel",
+                                   "achieved": flops_evs / t_evs_s / 1e12, "peak": pk,
+                                   "unit": "TFLOP/s", "frac": flops_evs / t_evs_s / 1e12 / pk,
+                                   "traffic": None, "peak_source": src,
+                                   "work": "%d MAC per pixel-step (4 x conv3x3 C%d + projection)"
+                                           % (macs, C)}
     if rank != 0:
         return
 
