@@ -29,6 +29,7 @@
 #ifndef EVENTTRACER_H
 #define EVENTTRACER_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -168,6 +169,54 @@ typedef struct {
 int et_evsnet_forward(const float* logl, int32_t F, const et_evsnet_weights* net,
                       et_evsnet_state* state, int32_t t0, et_event* events, int64_t cap,
                       int64_t* n_events, float* I_out, int8_t* spikes, void* stream);
+
+/* ------------------------------------------------------------------ training
+ * The learned form: EvSNet (plain stack of 3x3 convolutions, <= 16 channels,
+ * FP32 weights) trained on B clips of K steps.  Inputs are log frames
+ * logl [B][K+1][H][W] (device, FP32; step k uses X = l_{k+1} - l_k, Eq. 1) and
+ * targets E [B][K][H][W] (device, FP32 signed event counts per step).
+ * Spikes follow Eq. 3 read as S_on = Theta(V' - Vth), S_off = Theta(-V' - Vth);
+ * the backward uses the surrogate of Eq. 4, s(x) = (alpha/2) / (1 + (pi alpha x / 2)^2),
+ * on both thresholds and differentiates the reset.  The membrane starts at 0.
+ * Backpropagation through time keeps V at the start of every segment of
+ * ckpt_every (<= 32) steps and recomputes each segment in the backward. */
+typedef struct { int32_t B, K, H, W, ckpt_every; } et_train_shape;
+
+/* Bytes of the caller-allocated device workspace the two calls below need:
+ * the activations of one segment plus its gradients (about
+ * (2 n_layers + 2) C B ckpt_every H W floats). */
+int et_train_workspace_bytes(const et_evsnet_weights* net, const et_train_shape* shape,
+                             size_t* bytes);
+
+/* Forward over the batch.  Outputs (device): spikes int8 [B][K][H][W] (S_on - S_off),
+ * optional S_on / S_off float [B][K][H][W] (both or neither), V_ckpt float
+ * [B][ceil(K / ckpt_every)][H][W], optional I_out float [B][K][H][W].
+ * Errors: ET_ERR_ARG, ET_ERR_UNIMPLEMENTED (form other than a 3x3 stack, C > 16,
+ * dtype other than ET_F32, ckpt_every > 32), ET_ERR_CUDA. */
+int et_evsnet_train_forward(const float* logl, const et_train_shape* shape,
+                            const et_evsnet_weights* net, int8_t* spikes, float* S_on,
+                            float* S_off, float* V_ckpt, float* I_out, void* workspace,
+                            size_t workspace_bytes, void* stream);
+
+/* Eq. 7-11: per pixel, for each polarity, half the sum of the 1-D EMD of the
+ * sequences and of the reversed sequences (EMD(E, S) = (1/K) sum_i |cumsum(S - E)_i|),
+ * plus lambda |sum |S| - sum |E||; averaged over the B H W pixels.
+ * loss: device float [3] = (total, EMD part, count part); dS_on / dS_off: device
+ * float [B][K][H][W] gradients of the total.  Errors: ET_ERR_ARG, ET_ERR_CUDA. */
+int et_emd_count_loss(const int8_t* spikes, const float* E, const et_train_shape* shape,
+                      float lambda, float* loss, float* dS_on, float* dS_off, void* stream);
+
+/* Backward through BiLIF and the convolutions; gradients are ADDED to grad_w /
+ * grad_b (device, packed like the weights; zero them first).  Errors as forward. */
+int et_evsnet_train_backward(const float* logl, const et_train_shape* shape,
+                             const et_evsnet_weights* net, const float* V_ckpt,
+                             const float* dS_on, const float* dS_off, float alpha, float* grad_w,
+                             float* grad_b, void* workspace, size_t workspace_bytes, void* stream);
+
+/* Adam (Kingma & Ba 2015) with bias correction, FP32, in place on p, m, v (device, n).
+ * step >= 1 is the 1-based update count.  Errors: ET_ERR_ARG, ET_ERR_CUDA. */
+int et_adam_step(float* p, const float* g, float* m, float* v, int64_t n, float lr, float beta1,
+                 float beta2, float eps, int32_t step, void* stream);
 
 /* ------------------------------------------------------------------ metrics
  * Size of a maximum matching between two event lists (host pointers): events

@@ -41,6 +41,11 @@ class et_evsnet_state(C.Structure):
                 ("H", C.c_int32), ("W", C.c_int32), ("initialized", C.c_int32)]
 
 
+class et_train_shape(C.Structure):
+    _fields_ = [("B", C.c_int32), ("K", C.c_int32), ("H", C.c_int32), ("W", C.c_int32),
+                ("ckpt_every", C.c_int32)]
+
+
 EVENT_BYTES = 12
 
 # name -> (restype, argtypes); every symbol include/eventtracer.h declares
@@ -52,6 +57,11 @@ SIGNATURES = {
     "et_render_frames": (i32, [P, P, i32, i32, i32, i32, i32, i32, u64, P, P, i32, f32, P, P]),
     "et_threshold_events": (i32, [P, i32, i32, i32, f32, i32, P, i32, P, i64, P, P]),
     "et_evsnet_forward": (i32, [P, i32, P, P, i32, P, i64, P, P, P, P]),
+    "et_train_workspace_bytes": (i32, [P, P, P]),
+    "et_evsnet_train_forward": (i32, [P, P, P, P, P, P, P, P, P, C.c_size_t, P]),
+    "et_emd_count_loss": (i32, [P, P, P, f32, P, P, P, P]),
+    "et_evsnet_train_backward": (i32, [P, P, P, P, P, P, f32, P, P, P, C.c_size_t, P]),
+    "et_adam_step": (i32, [P, P, P, P, i64, f32, f32, f32, f32, i32, P]),
     "et_event_matches": (i32, [P, i64, P, i64, i32, P]),
     "et_status_str": (C.c_char_p, [i32]),
 }
