@@ -56,16 +56,8 @@ def parse():
 
 def load_net(dtype):
     """Trained EvSNet weights if present, else random-init weights of the same shape."""
-    import numpy as np
-    from paper_2508_18071_gb300 import api, inputs
-    path = os.path.join(ROOT, "paper_2508_18071_gb300", "weights", "evsnet_city.npz")
-    if os.path.exists(path):
-        z = np.load(path)
-        d = {k: (z[k].item() if z[k].ndim == 0 else z[k]) for k in z.files}
-        d["trained"] = True
-    else:
-        d = inputs.random_evsnet(0, 4, 16, 1, 3, seed=12, vth=0.5, beta=0.9)
-        d["trained"] = False
+    from paper_2508_18071_gb300 import api
+    _, d = load_net_host()
     return api.EvsNetDev.from_dict(d, dtype), d
 
 
@@ -207,14 +199,13 @@ def run_reference(args):
 
 
 def load_net_host():
-    import numpy as np
-    from paper_2508_18071_gb300 import inputs
+    from paper_2508_18071_gb300 import inputs, train_evsnet
     path = os.path.join(ROOT, "paper_2508_18071_gb300", "weights", "evsnet_city.npz")
     if os.path.exists(path):
-        z = np.load(path)
-        d = {k: (z[k].item() if z[k].ndim == 0 else z[k]) for k in z.files}
-        return None, d
-    return None, inputs.random_evsnet(0, 4, 16, 1, 3, seed=12, vth=0.5, beta=0.9)
+        return None, train_evsnet.load(path)
+    d = inputs.random_evsnet(0, 4, 16, 1, 3, seed=12, vth=0.5, beta=0.9)
+    d["trained"] = False
+    return None, d
 
 
 def main():
