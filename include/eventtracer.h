@@ -213,6 +213,28 @@ int et_evsnet_train_backward(const float* logl, const et_train_shape* shape,
                              const float* dS_on, const float* dS_off, float alpha, float* grad_w,
                              float* grad_b, void* workspace, size_t workspace_bytes, void* stream);
 
+/* et_evsnet_train_backward without a workspace argument, for callers that
+ * cannot allocate device memory: e.g. a plugin inside a framework whose own
+ * allocator owns all device memory, or a loop that must not call cudaMalloc /
+ * cudaFree because they can synchronise the device.  The paper has no
+ * counterpart; this is a deployment convenience of the library.
+ * The scratch is one array of et_train_static_workspace_capacity() bytes
+ * (32 MiB) compiled into the library; every device that loads the library
+ * holds it until the process exits.  Shapes needing more scratch than that
+ * (see et_train_workspace_bytes) are rejected with ET_ERR_CAPACITY.  The call
+ * itself allocates nothing.  The first call on a device looks up the array's
+ * device address (that device must be current); make that first call before
+ * any stream capture begins.  All calls share the one array and it keeps the
+ * previous call's contents (the call clears what must start at zero), so two
+ * calls whose execution overlaps on the GPU -- e.g. on different streams --
+ * race and give wrong gradients: serialise them.  Results, errors and the
+ * meaning of every other argument are those of et_evsnet_train_backward. */
+int et_evsnet_train_backward_static(const float* logl, const et_train_shape* shape,
+                                    const et_evsnet_weights* net, const float* V_ckpt,
+                                    const float* dS_on, const float* dS_off, float alpha,
+                                    float* grad_w, float* grad_b, void* stream);
+size_t et_train_static_workspace_capacity(void);
+
 /* Adam (Kingma & Ba 2015) with bias correction, FP32, in place on p, m, v (device, n).
  * step >= 1 is the 1-based update count.  Errors: ET_ERR_ARG, ET_ERR_CUDA. */
 int et_adam_step(float* p, const float* g, float* m, float* v, int64_t n, float lr, float beta1,

@@ -61,6 +61,8 @@ SIGNATURES = {
     "et_evsnet_train_forward": (i32, [P, P, P, P, P, P, P, P, P, C.c_size_t, P]),
     "et_emd_count_loss": (i32, [P, P, P, f32, P, P, P, P]),
     "et_evsnet_train_backward": (i32, [P, P, P, P, P, P, f32, P, P, P, C.c_size_t, P]),
+    "et_evsnet_train_backward_static": (i32, [P, P, P, P, P, P, f32, P, P, P]),
+    "et_train_static_workspace_capacity": (C.c_size_t, []),
     "et_adam_step": (i32, [P, P, P, P, i64, f32, f32, f32, f32, i32, P]),
     "et_event_matches": (i32, [P, i64, P, i64, i32, P]),
     "et_status_str": (C.c_char_p, [i32]),

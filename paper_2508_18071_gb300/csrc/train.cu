@@ -15,6 +15,7 @@
 // s(x) = (alpha / 2) / (1 + (pi alpha x / 2)^2); reset V = V' - r (S_on - S_off)
 // is differentiated (not detached).
 #include <algorithm>
+#include <mutex>
 #include "et_internal.cuh"
 #include "evsnet_common.h"
 #include "train_api.h"
@@ -577,4 +578,56 @@ extern "C" int et_adam_step(float* p, const float* g, float* m, float* v, int64_
                                                                              eps, bc1, bc2);
   ET_CHECK_LAUNCH();
   return ET_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Backward without a caller workspace.
+//
+// Some callers cannot hand the library a device workspace: a plugin that lives
+// inside a host framework whose caching allocator owns all device memory and
+// forbids side allocations, or a loop that must not call cudaMalloc / cudaFree
+// because those calls may synchronise the whole device.  For them this entry
+// point runs the same backward with its scratch in a fixed array compiled into
+// the library.  The array exists once per device that loads the library and is
+// kept until the process exits.
+namespace {
+constexpr size_t kStaticWorkspaceBytes = (size_t)32 << 20;   // 32 MiB
+constexpr int kMaxDevices = 64;
+std::mutex g_static_ws_mutex;
+void* g_static_ws[kMaxDevices] = {};
+}  // namespace
+
+// Device memory; host code must not use this name as an address (on the host it
+// only stands for the symbol).  Its device address comes from cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_static_workspace[kStaticWorkspaceBytes];
+
+extern "C" size_t et_train_static_workspace_capacity(void) { return kStaticWorkspaceBytes; }
+
+extern "C" int et_evsnet_train_backward_static(const float* logl, const et_train_shape* sh,
+                                               const et_evsnet_weights* net, const float* V_ckpt,
+                                               const float* dS_on, const float* dS_off, float alpha,
+                                               float* grad_w, float* grad_b, void* stream) {
+  int rc = check(net, sh);
+  if (rc != ET_OK) return rc;
+  Workspace ws{};
+  layout(net, sh, nullptr, &ws);
+  if (ws.bytes > kStaticWorkspaceBytes) return ET_ERR_CAPACITY;   // shape too large for the array
+  int dev = 0;
+  ET_CHECK_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return ET_ERR_ARG;
+  void* base = nullptr;
+  {
+    // first call on this device (with it current): look up the array's device address
+    std::lock_guard<std::mutex> lock(g_static_ws_mutex);
+    if (!g_static_ws[dev]) {
+      void* p = nullptr;
+      ET_CHECK_CUDA(cudaGetSymbolAddress(&p, g_static_workspace));
+      g_static_ws[dev] = p;
+    }
+    base = g_static_ws[dev];
+  }
+  // the backward clears the part of the scratch that must start at zero (the
+  // carried membrane gradient) and overwrites the rest before reading it
+  return et_evsnet_train_backward(logl, sh, net, V_ckpt, dS_on, dS_off, alpha, grad_w, grad_b, base,
+                                  kStaticWorkspaceBytes, stream);
 }
