@@ -110,6 +110,16 @@ int et_render_frames(const et_scene* scene, const et_camera* cams, int32_t n_fra
                      int32_t max_depth, uint64_t seed, float* rgb, float* logl,
                      int32_t log_mode, float log_param, int32_t* records, void* stream);
 
+/* Schedule used by et_render_frames on this scene; both compute identical
+ * outputs.  ET_RENDER_WAVEFRONT (default): paths advance one segment at a time
+ * through compacted ray queues traced by persistent warps that refill idle
+ * lanes; it keeps a device workspace in the scene (up to ~1.3 GB for 8M paths
+ * in flight), allocated by the first call that needs it and kept until
+ * et_scene_free.  ET_RENDER_MEGAKERNEL: one thread per pixel, no workspace.
+ * Errors: ET_ERR_ARG. */
+enum { ET_RENDER_WAVEFRONT = 0, ET_RENDER_MEGAKERNEL = 1 };
+int et_render_set_mode(et_scene* scene, int32_t mode);
+
 /* ---------------------------------------------------------- threshold events
  * Sec. 3.1 contrast-threshold model (the method without EvSNet, the 256-SPP
  * reference and the training target).  Per pixel, in FP64:

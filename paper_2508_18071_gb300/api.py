@@ -57,6 +57,10 @@ class Scene:
         L.check("et_build_scene", st)
         self._h = h
 
+    def set_mode(self, mode: int):
+        """ET_RENDER_WAVEFRONT (default) or ET_RENDER_MEGAKERNEL."""
+        L.check("et_render_set_mode", L.load().et_render_set_mode(self._h, int(mode)))
+
     def info(self):
         n, nn, sah = C.c_int64(), C.c_int64(), C.c_double()
         L.check("et_scene_info", L.load().et_scene_info(self._h, C.byref(n), C.byref(nn), C.byref(sah)))

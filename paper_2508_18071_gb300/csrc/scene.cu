@@ -289,6 +289,7 @@ extern "C" void et_scene_free(et_scene* s) {
   if (!s) return;
   cudaFree(s->d_tris); cudaFree(s->d_nodes); cudaFree(s->d_mats); cudaFree(s->d_lights);
   cudaFree(s->d_cams);
+  cudaFree(s->wf_mem);
   delete s;
 }
 
