@@ -85,6 +85,11 @@ int et_build_scene(const float* tris, const uint32_t* tri_mat, int64_t n_tris,
                    const et_quad_light* lights, int32_t n_lights, float env,
                    et_scene** out, void* stream);
 void et_scene_free(et_scene* scene);
+/* Which builder produced the hierarchy: ET_BVH_GPU (binned SAH on the device,
+ * the default) or ET_BVH_HOST (the same heuristic on the host, used when the
+ * device tree would be deeper than the traversal stack's 64 levels). */
+enum { ET_BVH_GPU = 0, ET_BVH_HOST = 1 };
+int et_scene_builder(const et_scene* scene);
 /* Triangle count (including the lights' triangles), BVH node count and its SAH
  * cost (C_trav = C_isect = 1, normalised by the root's surface area). */
 int et_scene_info(const et_scene* scene, int64_t* n_tris, int64_t* n_nodes, double* sah_cost);

@@ -16,6 +16,7 @@ ET_LOG_EPS, ET_LOG_PAPER = 0, 1
 ET_F32, ET_BF16, ET_FP8 = 0, 1, 2
 ET_NET_STACK, ET_NET_RESIDUAL = 0, 1
 ET_RENDER_WAVEFRONT, ET_RENDER_MEGAKERNEL = 0, 1
+ET_BVH_GPU, ET_BVH_HOST = 0, 1
 
 
 class et_material(C.Structure):
@@ -55,6 +56,7 @@ SIGNATURES = {
     "et_build_scene": (i32, [P, P, i64, P, i32, P, i32, f32, P, P]),
     "et_scene_free": (None, [P]),
     "et_scene_info": (i32, [P, P, P, P]),
+    "et_scene_builder": (i32, [P]),
     "et_render_frames": (i32, [P, P, i32, i32, i32, i32, i32, i32, u64, P, P, i32, f32, P, P]),
     "et_render_set_mode": (i32, [P, i32]),
     "et_threshold_events": (i32, [P, i32, i32, i32, f32, i32, P, i32, P, i64, P, P]),

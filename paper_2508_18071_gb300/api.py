@@ -64,7 +64,8 @@ class Scene:
     def info(self):
         n, nn, sah = C.c_int64(), C.c_int64(), C.c_double()
         L.check("et_scene_info", L.load().et_scene_info(self._h, C.byref(n), C.byref(nn), C.byref(sah)))
-        return {"n_tris": n.value, "n_nodes": nn.value, "sah_cost": sah.value}
+        builder = "gpu" if L.load().et_scene_builder(self._h) == L.ET_BVH_GPU else "host"
+        return {"n_tris": n.value, "n_nodes": nn.value, "sah_cost": sah.value, "builder": builder}
 
     def free(self):
         if getattr(self, "_h", None):

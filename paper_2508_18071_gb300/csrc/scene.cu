@@ -13,32 +13,14 @@
 #include <cmath>
 #include "et_internal.cuh"
 #include "scene_internal.h"
+#include "bvh_build.h"
 
 static thread_local cudaError_t g_last_cuda = cudaSuccess;
 void et_set_last_cuda_error(cudaError_t e) { g_last_cuda = e; }
 
 namespace {
 
-struct Box {
-  float lo[3], hi[3];
-  void reset() { for (int k = 0; k < 3; ++k) { lo[k] = FLT_MAX; hi[k] = -FLT_MAX; } }
-  void grow(const Box& b) {
-    for (int k = 0; k < 3; ++k) { lo[k] = std::min(lo[k], b.lo[k]); hi[k] = std::max(hi[k], b.hi[k]); }
-  }
-  void grow(const float* p) {
-    for (int k = 0; k < 3; ++k) { lo[k] = std::min(lo[k], p[k]); hi[k] = std::max(hi[k], p[k]); }
-  }
-  double area() const {
-    double dx = (double)hi[0] - lo[0], dy = (double)hi[1] - lo[1], dz = (double)hi[2] - lo[2];
-    if (dx < 0 || dy < 0 || dz < 0) return 0.0;
-    return 2.0 * (dx * dy + dy * dz + dz * dx);
-  }
-};
-
-struct BuildNode { Box box; int left, right, first, count; };
-
-constexpr int kBins = 32;
-constexpr int kLeafMax = 4;
+constexpr int kBins = kSahBins;
 
 struct Builder {
   const std::vector<Box>& tb;
@@ -201,13 +183,26 @@ extern "C" int et_build_scene(const float* tris, const uint32_t* tri_mat, int64_
   int root_ref = -1;   // an empty leaf: first 0, count 0
   double sah = 0.0;
   int64_t n_nodes = 0;
+  int builder = ET_BVH_GPU;
   if (n > 0) {
-    Builder B(tb, cent, n);
-    B.build_all(n);
     // the traversal kernels keep at most one pending subtree per level on a
-    // 64-entry stack; deeper hierarchies are refused rather than overflowed
-    if (B.max_depth > kMaxBvhDepth) return ET_ERR_UNIMPLEMENTED;
-    const auto& bn = B.nodes;
+    // 64-entry stack: the GPU build is used unless its tree is deeper, then the
+    // host build; deeper hierarchies are refused rather than overflowed
+    std::vector<BuildNode> bn_store;
+    std::vector<int> perm;
+    int depth = 0;
+    const int grc = gpu_binned_sah(v.data(), n, stream, bn_store, perm, depth);
+    if (grc != ET_OK || depth > kMaxBvhDepth) {
+      if (grc == ET_ERR_CUDA || grc == ET_ERR_OOM) cudaGetLastError();
+      builder = ET_BVH_HOST;
+      Builder B(tb, cent, n);
+      B.build_all(n);
+      bn_store.swap(B.nodes);
+      perm.swap(B.idx);
+      depth = B.max_depth;
+    }
+    if (depth > kMaxBvhDepth) return ET_ERR_UNIMPLEMENTED;
+    const auto& bn = bn_store;
     std::vector<int> inner_index(bn.size(), -1);
     int ni = 0;
     for (size_t i = 0; i < bn.size(); ++i) if (bn[i].count == 0) inner_index[i] = ni++;
@@ -228,7 +223,7 @@ extern "C" int et_build_scene(const float* tris, const uint32_t* tri_mat, int64_
     n_nodes = (int64_t)bn.size();
     root_ref = ref_of(bn, inner_index, 0);
     for (int64_t s = 0; s < n; ++s) {
-      int t = B.idx[s];
+      int t = perm[s];
       const float* p = &v[(size_t)t * 9];
       uint32_t prim = (uint32_t)t, mat = m[t];
       float pf, mf;
@@ -250,7 +245,7 @@ extern "C" int et_build_scene(const float* tris, const uint32_t* tri_mat, int64_
   }
 
   et_scene* s = new et_scene();
-  s->n_tris = n; s->n_nodes = n_nodes; s->sah = sah;
+  s->n_tris = n; s->n_nodes = n_nodes; s->sah = sah; s->builder = builder;
   auto fail = [&](int code) { et_scene_free(s); return code; };
   cudaError_t e;
 #define ET_SCENE_ALLOC(ptr, bytes)                                   \
@@ -292,6 +287,8 @@ extern "C" void et_scene_free(et_scene* s) {
   cudaFree(s->wf_mem);
   delete s;
 }
+
+extern "C" int et_scene_builder(const et_scene* s) { return s ? s->builder : -1; }
 
 extern "C" int et_scene_info(const et_scene* s, int64_t* n_tris, int64_t* n_nodes, double* sah) {
   if (!s) return ET_ERR_ARG;

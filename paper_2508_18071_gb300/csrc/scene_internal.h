@@ -13,6 +13,7 @@ struct et_scene {
   double sah = 0.0;
   et_scene_dev dev{};
   int render_mode = ET_RENDER_WAVEFRONT;
+  int builder = ET_BVH_GPU;
   void* wf_mem = nullptr;        // wavefront queues and path state, grown on demand
   int64_t wf_cap = 0, wf_acc_cap = 0;
 };
