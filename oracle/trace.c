@@ -285,7 +285,7 @@ static void closest(const orc_scene* s, const double* o, const double* d, double
       const node_t* nd = &s->nodes[stack[--sp]];
       double tn;
       if (nv) ++*nv;
-      if (!box_hit(&r, nd, found ? best : tmax, &tn)) continue;
+      if (!box_hit(&r, nd, found ? best * (1.0 + 2.0 * GAMMA3) : tmax, &tn)) continue;
       if (nd->count > 0) {
         for (int32_t i = 0; i < nd->count; ++i) {
           int32_t p = s->perm[nd->first + i];
@@ -295,8 +295,8 @@ static void closest(const orc_scene* s, const double* o, const double* d, double
         }
       } else {
         double tl, tr;
-        int hl = box_hit(&r, &s->nodes[nd->left], found ? best : tmax, &tl);
-        int hr = box_hit(&r, &s->nodes[nd->right], found ? best : tmax, &tr);
+        int hl = box_hit(&r, &s->nodes[nd->left], found ? best * (1.0 + 2.0 * GAMMA3) : tmax, &tl);
+        int hr = box_hit(&r, &s->nodes[nd->right], found ? best * (1.0 + 2.0 * GAMMA3) : tmax, &tr);
         if (hl && hr) {
           if (tl <= tr) { stack[sp++] = nd->right; stack[sp++] = nd->left; }
           else { stack[sp++] = nd->left; stack[sp++] = nd->right; }

@@ -106,11 +106,16 @@ struct Traversal {
 
   static constexpr int kDone = INT_MIN;   // no subtree left (leaf references are > INT_MIN)
 
+  // Culling distance: a subtree is skipped only if it starts beyond the best hit
+  // by more than the rounding of the slab entry distance, so that a triangle at
+  // exactly the best distance with a lower index (the tie rule) is still tested.
+  __device__ __forceinline__ float cull() const { return h.t * (1.0f + 2.0f * kGamma3); }
+
   // take the nearest pending subtree that can still hold a closer hit
   __device__ __forceinline__ void pop() {
     while (sp > 0) {
       --sp;
-      if (st_t[sp] <= h.t) { ref = st_ref[sp]; return; }
+      if (st_t[sp] <= cull()) { ref = st_ref[sp]; return; }
     }
     ref = kDone;
   }
@@ -124,8 +129,8 @@ struct Traversal {
     const float4 a = __ldg(np), b = __ldg(np + 1), c = __ldg(np + 2);
     const int4 d = __ldg(reinterpret_cast<const int4*>(np + 3));
     float t0, t1;
-    const bool h0 = slab(r, a.x, a.y, a.z, a.w, b.x, b.y, h.t, t0);
-    const bool h1 = slab(r, b.z, b.w, c.x, c.y, c.z, c.w, h.t, t1);
+    const bool h0 = slab(r, a.x, a.y, a.z, a.w, b.x, b.y, cull(), t0);
+    const bool h1 = slab(r, b.z, b.w, c.x, c.y, c.z, c.w, cull(), t1);
     if (h0 && h1) {
       const bool first0 = t0 <= t1;
       st_ref[sp] = first0 ? d.y : d.x;
@@ -164,8 +169,8 @@ struct Traversal {
       const float4 a = __ldg(np), b = __ldg(np + 1), c = __ldg(np + 2);
       const int4 d = __ldg(reinterpret_cast<const int4*>(np + 3));
       float t0, t1;
-      const bool h0 = slab(r, a.x, a.y, a.z, a.w, b.x, b.y, h.t, t0);
-      const bool h1 = slab(r, b.z, b.w, c.x, c.y, c.z, c.w, h.t, t1);
+      const bool h0 = slab(r, a.x, a.y, a.z, a.w, b.x, b.y, cull(), t0);
+      const bool h1 = slab(r, b.z, b.w, c.x, c.y, c.z, c.w, cull(), t1);
       if (h0 && h1) {
         const bool first0 = t0 <= t1;
         st_ref[sp] = first0 ? d.y : d.x;
@@ -193,7 +198,7 @@ struct Traversal {
     // pop the nearest pending subtree that can still hold a closer hit
     while (sp > 0) {
       --sp;
-      if (st_t[sp] <= h.t) { ref = st_ref[sp]; return true; }
+      if (st_t[sp] <= cull()) { ref = st_ref[sp]; return true; }
     }
     return false;
   }
