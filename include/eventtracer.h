@@ -267,6 +267,10 @@ int et_event_matches(const et_event* a, int64_t n_a, const et_event* b, int64_t 
 
 const char* et_status_str(int status);
 
+/* Number of CUDA kernels the library has launched in this process (all
+ * devices, all calls); a monotone counter for instrumentation. */
+uint64_t et_kernel_launches(void);
+
 #ifdef __cplusplus
 }
 #endif

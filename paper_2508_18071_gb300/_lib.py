@@ -70,6 +70,7 @@ SIGNATURES = {
     "et_adam_step": (i32, [P, P, P, P, i64, f32, f32, f32, f32, i32, P]),
     "et_event_matches": (i32, [P, i64, P, i64, i32, P]),
     "et_status_str": (C.c_char_p, [i32]),
+    "et_kernel_launches": (u64, []),
 }
 
 _lib = None

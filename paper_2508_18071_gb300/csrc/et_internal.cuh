@@ -14,7 +14,14 @@
     }                                                         \
   } while (0)
 
-#define ET_CHECK_LAUNCH() ET_CHECK_CUDA(cudaGetLastError())
+// every kernel launch of the library is followed by this: counts it, checks it
+#define ET_CHECK_LAUNCH()           \
+  do {                              \
+    et_count_launch();              \
+    ET_CHECK_CUDA(cudaGetLastError()); \
+  } while (0)
+
+void et_count_launch();
 
 void et_set_last_cuda_error(cudaError_t e);
 

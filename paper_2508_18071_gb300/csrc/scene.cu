@@ -6,6 +6,7 @@
 // only the camera) with a binned surface-area heuristic: 32 centroid bins per
 // axis, leaves of at most 4 triangles, nodes storing both children's boxes so
 // that one 64-byte fetch serves two box tests.
+#include <atomic>
 #include <vector>
 #include <algorithm>
 #include <cstring>
@@ -17,6 +18,10 @@
 
 static thread_local cudaError_t g_last_cuda = cudaSuccess;
 void et_set_last_cuda_error(cudaError_t e) { g_last_cuda = e; }
+
+static std::atomic<uint64_t> g_launches{0};
+void et_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+extern "C" uint64_t et_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 namespace {
 
