@@ -48,7 +48,9 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-rows", type=int, default=720, help="oracle sample: rows per frame")
     p.add_argument("--cpu-frames", type=int, default=2, help="oracle sample: frames")
-    p.add_argument("--evsnet-dtype", default="bf16", choices=["f32", "bf16"])
+    p.add_argument("--evsnet-dtype", default="bf16", choices=["f32", "bf16", "fp8"])
+    p.add_argument("--no-sweep", action="store_true",
+                   help="skip the EvSNet precision sweep (FP32 / BF16 / FP8) after the timed region")
     p.add_argument("--width", type=int, default=1280, help="smaller sizes: profiling cases only")
     p.add_argument("--height", type=int, default=720)
     return p.parse_args()
@@ -198,6 +200,39 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def precision_sweep(api, _lib, net_d, logl, stream, reps=5):
+    """EvSNet alone on the last step's rendered frames in each precision: device
+    time per frame, tensor throughput, and events against the FP32 path (F1 with
+    no spatial or temporal tolerance)."""
+    import torch
+    F, H, W = logl.shape
+    C, Lr = net_d["C"], net_d["n_layers"]
+    flops = 2.0 * (9 * C + (Lr - 1) * 9 * C * C + C) * H * W * (F - 1)
+    out, ev_ref = {}, None
+    for name, dt in (("f32", _lib.ET_F32), ("bf16", _lib.ET_BF16), ("fp8", _lib.ET_FP8)):
+        net = api.EvsNetDev.from_dict(net_d, dt)
+        buf = api.EventBuffer(F * H * W)
+        ts = []
+        for r in range(reps + 1):
+            st = api.EvsStateDev(net, H, W)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            api.evsnet_forward(logl, net, st, t0=0, buf=buf)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if r > 0:
+                ts.append(e0.elapsed_time(e1))
+        ev = buf.host()
+        if ev_ref is None:
+            ev_ref = ev
+        ms = statistics.median(ts)
+        out[name] = {"ms_per_frame": ms / (F - 1), "tflops": flops / (ms / 1e3) / 1e12,
+                     "events": len(ev), "f1_vs_f32": api.event_f1(ev, ev_ref, 0)}
+    out["frames"] = F - 1
+    out["note"] = "first frame only sets the state; median of %d calls" % reps
+    return out
+
+
 def load_net_host():
     from paper_2508_18071_gb300 import inputs, train_evsnet
     path = os.path.join(ROOT, "paper_2508_18071_gb300", "weights", "evsnet_city.npz")
@@ -232,7 +267,7 @@ def main():
     scene = inputs.city_block(seed=21)
     g = api.Scene(scene)
     info = g.info()
-    dtype = _lib.ET_BF16 if args.evsnet_dtype == "bf16" else _lib.ET_F32
+    dtype = {"f32": _lib.ET_F32, "bf16": _lib.ET_BF16, "fp8": _lib.ET_FP8}[args.evsnet_dtype]
     net, net_d = load_net(dtype)
     F = args.frames
     npix = W_ * H_
@@ -346,16 +381,22 @@ def main():
     pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(pk_path):
         peaks = json.load(open(pk_path))
-    if dtype == _lib.ET_BF16:
+    if dtype in (_lib.ET_BF16, _lib.ET_FP8):
         pk = peaks.get("bf16_tflops_sustained") or 1700.0
         src = "MEASURED_PEAKS bf16_tflops_sustained (of measured)" if "bf16_tflops_sustained" in peaks \
             else "fallback 1.7 PFLOP/s sustained"
+        if dtype == _lib.ET_FP8:
+            # nominal dense fp8 / bf16 ratio (4.5 / 2.25 PFLOP/s)
+            pk *= 2.0
+            src += " x 2 (nominal fp8 / bf16 ratio)"
         line["roofline_evsnet"] = {"bound": "tensor", "kernel": "evsnet_tc_kernel",
                                    "achieved": flops_evs / t_evs_s / 1e12, "peak": pk,
                                    "unit": "TFLOP/s", "frac": flops_evs / t_evs_s / 1e12 / pk,
                                    "traffic": None, "peak_source": src,
                                    "work": "%d MAC per pixel-step (4 x conv3x3 C%d + projection)"
                                            % (macs, C)}
+    if not args.no_sweep:
+        line["evsnet_precision_sweep"] = precision_sweep(api, _lib, net_d, logl, stream)
     if rank != 0:
         return
 

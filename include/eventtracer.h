@@ -149,7 +149,12 @@ int et_threshold_events(const float* logl, int32_t F, int32_t H, int32_t W, floa
  * Temporal taps are causal (tap kt-1 = current step); spatial padding is zero.
  * BiLIF (Eq. 2-3; fire on the pre-reset potential):
  *   V' = beta V + I;  S = +1 if V' >= vth, -1 if V' <= -vth, else 0;  V = V' - reset S.
- * dtype: ET_F32 (CUDA cores) or ET_BF16 (tensor cores, FP32 accumulation).
+ * dtype: ET_F32 (CUDA cores), ET_BF16 or ET_FP8 (tensor cores, FP32 accumulation).
+ *   ET_BF16 rounds the weights of layers 1.. and their inputs to BF16.
+ *   ET_FP8 rounds them to E4M3 after scaling: weights per output channel and
+ *   layer inputs per layer, 32x16 pixel tile and step, each by the power of two
+ *   that brings its absolute maximum to at most 448 (exact to undo).
+ *   Layer 0, the projection and BiLIF stay FP32 in both.
  */
 typedef struct {
   int32_t kind, n_layers, C, kt, ks;
@@ -179,8 +184,9 @@ typedef struct {
  *   I_out    device float [K][H][W] projection output (BiLIF input), or NULL
  *   spikes   device int8 [K][H][W] dense spikes, or NULL
  * K = F - 1 if the state was not initialized, else F.
- * Errors: ET_ERR_ARG, ET_ERR_UNIMPLEMENTED (C > 32, ks > 7, kt > 9, BF16 for a
- * shape the tensor-core kernel does not cover), ET_ERR_CUDA. */
+ * Errors: ET_ERR_ARG, ET_ERR_UNIMPLEMENTED (C > 32, ks > 7, kt > 9, BF16 or FP8
+ * for a shape the tensor-core kernel does not cover: it takes a plain stack of
+ * 2 to 6 layers of 3x3 spatial convolutions), ET_ERR_CUDA. */
 int et_evsnet_forward(const float* logl, int32_t F, const et_evsnet_weights* net,
                       et_evsnet_state* state, int32_t t0, et_event* events, int64_t cap,
                       int64_t* n_events, float* I_out, int8_t* spikes, void* stream);

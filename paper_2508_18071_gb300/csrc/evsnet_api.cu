@@ -1,5 +1,5 @@
 // et_evsnet_forward: argument checks and dispatch between the FP32 (CUDA core)
-// and BF16 (tensor core) EvSNet kernels.
+// and BF16 / FP8 (tensor core) EvSNet kernels.
 #include "et_internal.cuh"
 #include "evsnet_common.h"
 
@@ -26,8 +26,8 @@ extern "C" int et_evsnet_forward(const float* logl, int32_t F, const et_evsnet_w
   int rc;
   if (net->dtype == ET_F32)
     rc = et_evsnet_forward_f32(logl, F, net, st, t0, events, cap, n_events, I_out, spikes, stream);
-  else if (net->dtype == ET_BF16)
-    rc = et_evsnet_forward_bf16(logl, F, net, st, t0, events, cap, n_events, I_out, spikes, stream);
+  else if (net->dtype == ET_BF16 || net->dtype == ET_FP8)
+    rc = et_evsnet_forward_tc(logl, F, net, st, t0, events, cap, n_events, I_out, spikes, stream);
   else
     rc = ET_ERR_UNIMPLEMENTED;
   if (rc != ET_OK) return rc;
