@@ -7,9 +7,12 @@ same frames -- the project's stand-in for the paper's V2E ground truth
 kernels: checkpointed forward, EMD + count loss (Eq. 7-11), surrogate BPTT
 (Eq. 4) and Adam.
 
-The network starts as the identity EvSNet (its projection reproduces X, and
-with beta = 1 and Vth = reset = C the BiLIF unit is then exactly the threshold
-generator), i.e. as "the method without EvSNet", and learns to denoise.
+The network starts as the identity EvSNet (its projection reproduces X; with
+beta = 1 and Vth = reset = C the BiLIF unit is then exactly the threshold
+generator, i.e. "the method without EvSNet") and learns to denoise.  The
+default leak is beta = 0.9 (tau = 10 in the charge step of Eq. 2): without a
+leak any constant offset of the learned current integrates without bound and
+makes every pixel fire periodically, even on a static image.
 
     python -m paper_2508_18071_gb300.train_evsnet --scene city --out weights/evsnet_city.npz
 """
@@ -28,12 +31,12 @@ from . import api, inputs, training
 HERE = os.path.dirname(os.path.abspath(__file__))
 
 
-def identity_init(C=16, n_layers=4, vth=0.2, std=0.01, seed=0):
+def identity_init(C=16, n_layers=4, vth=0.2, std=0.01, seed=0, beta=0.9):
     """Identity 3x3 stack (channels 0/1 carry ReLU(+-X)) plus small noise."""
     d = inputs.identity_evsnet(0, n_layers, C, 1, 3, vth=vth)
     rng = np.random.default_rng(seed)
     d["w"] = (d["w"] + rng.normal(0, std, d["w"].shape)).astype(np.float32)
-    d["beta"] = 1.0
+    d["beta"] = float(beta)
     d["reset"] = vth
     return d
 
@@ -90,7 +93,7 @@ def make_clips(scene: api.Scene, scene_kind, seeds, n_frames, size, spp_in, spp_
 
 def train(scene_kind="city", n_clips=32, n_frames=65, size=128, spp_in=2, spp_ref=256,
           C_range=(0.2, 0.2), iters=300, batch=8, lr=3e-3, lam=0.01, C=16, n_layers=4, vth=0.2,
-          seed=0, log=print):
+          seed=0, beta=0.9, log=print):
     sc_dict = inputs.city_block(seed=21) if scene_kind == "city" else inputs.random_scene(seed=11)
     scene = api.Scene(sc_dict)
     t0 = time.time()
@@ -99,7 +102,7 @@ def train(scene_kind="city", n_clips=32, n_frames=65, size=128, spp_in=2, spp_re
     torch.cuda.synchronize()
     log("data: %d clips x %d frames x %dx%d in %.1f s, %.3f target events per pixel-step"
         % (n_clips, n_frames, size, size, time.time() - t0, float(E.abs().mean())))
-    T = training.Trainer(identity_init(C, n_layers, vth, seed=seed), lr=lr, lam=lam)
+    T = training.Trainer(identity_init(C, n_layers, vth, seed=seed, beta=beta), lr=lr, lam=lam)
     rng = np.random.default_rng(seed)
     hist = []
     t0 = time.time()
@@ -113,7 +116,7 @@ def train(scene_kind="city", n_clips=32, n_frames=65, size=128, spp_in=2, spp_re
     return T, hist
 
 
-def evaluate(net: dict, scene_kind="city", seeds=(900, 901), n_frames=33, size=96, spp_in=2,
+def evaluate(net: dict, scene_kind="city", seeds=(900, 901), n_frames=129, size=96, spp_in=2,
              spp_ref=256, C_thr=0.2, delta=1):
     """F1 and mean EMD of (trained EvSNet on low SPP) and (threshold on low SPP)
     against threshold events of 256-SPP renders, on held-out clips; plus the
@@ -187,12 +190,14 @@ def main():
     p.add_argument("--spp-ref", type=int, default=256, help="SPP of the target renders")
     p.add_argument("--c-min", type=float, default=0.2)
     p.add_argument("--c-max", type=float, default=0.2)
+    p.add_argument("--beta", type=float, default=0.9, help="BiLIF leak (1 - 1/tau)")
+    p.add_argument("--eval-frames", type=int, default=129)
     p.add_argument("--out", default=os.path.join(HERE, "weights", "evsnet_city.npz"))
     a = p.parse_args()
     T, hist = train(a.scene, a.clips, a.frames, a.size, a.spp_in, a.spp_ref, (a.c_min, a.c_max),
-                    a.iters, lr=a.lr, lam=a.lam)
+                    a.iters, lr=a.lr, lam=a.lam, beta=a.beta)
     net = T.net_dict()
-    ev = evaluate(net, a.scene)
+    ev = evaluate(net, a.scene, n_frames=a.eval_frames)
     print("held-out:", ev)
     os.makedirs(os.path.dirname(a.out), exist_ok=True)
     save(a.out, net, hist, ev)
