@@ -89,11 +89,11 @@ struct Hit { float t; int slot; uint32_t prim; };
 
 // Resumable traversal of the two-wide hierarchy: `step` processes one node or
 // one leaf and returns false once the ray is finished.  Pending subtrees sit on
-// a per-thread stack with their entry distances.
+// a per-thread stack of (reference, entry distance) pairs, one 8-byte access
+// per push or pop.
 template <bool kAnyHit>
 struct Traversal {
-  int st_ref[kStack];
-  float st_t[kStack];
+  int2 st[kStack];
   int sp;
   int ref;
   float tmax;
@@ -115,7 +115,8 @@ struct Traversal {
   __device__ __forceinline__ void pop() {
     while (sp > 0) {
       --sp;
-      if (st_t[sp] <= cull()) { ref = st_ref[sp]; return; }
+      const int2 e = st[sp];
+      if (__int_as_float(e.y) <= cull()) { ref = e.x; return; }
     }
     ref = kDone;
   }
@@ -133,8 +134,7 @@ struct Traversal {
     const bool h1 = slab(r, b.z, b.w, c.x, c.y, c.z, c.w, cull(), t1);
     if (h0 && h1) {
       const bool first0 = t0 <= t1;
-      st_ref[sp] = first0 ? d.y : d.x;
-      st_t[sp] = first0 ? t1 : t0;
+      st[sp] = make_int2(first0 ? d.y : d.x, __float_as_int(first0 ? t1 : t0));
       ++sp;
       ref = first0 ? d.x : d.y;
     } else if (h0) {
@@ -173,8 +173,7 @@ struct Traversal {
       const bool h1 = slab(r, b.z, b.w, c.x, c.y, c.z, c.w, cull(), t1);
       if (h0 && h1) {
         const bool first0 = t0 <= t1;
-        st_ref[sp] = first0 ? d.y : d.x;
-        st_t[sp] = first0 ? t1 : t0;
+        st[sp] = make_int2(first0 ? d.y : d.x, __float_as_int(first0 ? t1 : t0));
         ++sp;
         ref = first0 ? d.x : d.y;
         return true;
@@ -198,7 +197,8 @@ struct Traversal {
     // pop the nearest pending subtree that can still hold a closer hit
     while (sp > 0) {
       --sp;
-      if (st_t[sp] <= cull()) { ref = st_ref[sp]; return true; }
+      const int2 e = st[sp];
+      if (__int_as_float(e.y) <= cull()) { ref = e.x; return true; }
     }
     return false;
   }

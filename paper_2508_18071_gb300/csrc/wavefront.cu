@@ -100,8 +100,12 @@ __global__ void __launch_bounds__(256) wf_raygen(Args A) {
 
 // Persistent traversal with dynamic ray fetch.  kShadow: any-hit shadow rays
 // (queue sho/shd/shc), else closest-hit extension rays (queue qo/qd -> hit).
+// resident blocks of 128 threads per SM the register allocation aims for
+#ifndef ET_TRACE_MIN_BLOCKS
+#define ET_TRACE_MIN_BLOCKS 12
+#endif
 template <bool kShadow>
-__global__ void __launch_bounds__(128) wf_trace(Args A, int cur, int b) {
+__global__ void __launch_bounds__(128, ET_TRACE_MIN_BLOCKS) wf_trace(Args A, int cur, int b) {
   const uint32_t n = A.ctr[kShadow ? C_NSH : (C_NRAY0 + cur)];
   uint32_t* fetch = A.ctr + (kShadow ? C_FETCH_SH : C_FETCH);
   const unsigned lane = threadIdx.x & 31u;
