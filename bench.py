@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--cpu-rows", type=int, default=720, help="oracle sample: rows per frame")
     p.add_argument("--cpu-frames", type=int, default=2, help="oracle sample: frames")
     p.add_argument("--evsnet-dtype", default="bf16", choices=["f32", "bf16", "fp8"])
+    p.add_argument("--bvh", default=None, choices=["gpu", "host", "sweep"],
+                   help="hierarchy builder (default: the library's)")
     p.add_argument("--no-sweep", action="store_true",
                    help="skip the EvSNet precision sweep (FP32 / BF16 / FP8) after the timed region")
     p.add_argument("--width", type=int, default=1280, help="smaller sizes: profiling cases only")
@@ -265,8 +267,10 @@ def main():
     props = torch.cuda.get_device_properties(dev)
 
     scene = inputs.city_block(seed=21)
-    g = api.Scene(scene)
+    tb0 = time.perf_counter()
+    g = api.Scene(scene, builder=args.bvh)
     info = g.info()
+    info["build_s"] = time.perf_counter() - tb0
     dtype = {"f32": _lib.ET_F32, "bf16": _lib.ET_BF16, "fp8": _lib.ET_FP8}[args.evsnet_dtype]
     net, net_d = load_net(dtype)
     F = args.frames
@@ -354,7 +358,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 render + %s EvSNet" % ("f32" if dtype == _lib.ET_F32 else "bf16"),
+        "dtype": "f32 render + %s EvSNet" % args.evsnet_dtype,
         "data": "synthetic (procedural city block, random-init EvSNet)" if not net_d.get("trained")
                 else "synthetic (procedural city block, EvSNet trained on procedural clips)",
         "config": {"workload": "city block %d tris (BVH %d nodes), %dx%d, 1 kHz, %d spp, depth 5, "
@@ -362,6 +366,8 @@ def main():
                                                                        W_, H_, args.spp, net.n_layers,
                                                                        net.ks, net.ks, net.C),
                    "frames_per_step": F, "l2": "flushed between steps (256 MB write)",
+                   "bvh": {"builder": info["builder"], "sah_cost": info["sah_cost"],
+                           "build_s": info["build_s"]},
                    "parallelism": "replicas: each rank renders its own path segment"},
         "wall_s_timed": wall,
         "gpu_launches": launches,

@@ -71,8 +71,9 @@ typedef struct { float pos[3]; float rot[9]; float vfov_deg; } et_camera;
 typedef struct { uint16_t x, y; uint32_t t; int8_t p; uint8_t pad[3]; } et_event;
 
 /* ---------------------------------------------------------------------- scene
- * Builds the scene: copies the geometry to the device and builds a binned-SAH
- * bounding volume hierarchy (two-wide, leaves of at most 4 triangles).
+ * Builds the scene: copies the geometry to the device and builds a surface-area
+ * heuristic bounding volume hierarchy (two-wide, leaves of at most 4
+ * triangles) with the default builder ET_BVH_DEFAULT (see et_build_scene_with).
  *   tris      host float [n_tris][9]: v0, v1, v2 of each triangle
  *   tri_mat   host uint32 [n_tris]: material index (< n_mats)
  *   mats      host [n_mats];  lights host [n_lights] (may be 0)
@@ -84,11 +85,24 @@ int et_build_scene(const float* tris, const uint32_t* tri_mat, int64_t n_tris,
                    const et_material* mats, int32_t n_mats,
                    const et_quad_light* lights, int32_t n_lights, float env,
                    et_scene** out, void* stream);
+/* Hierarchy builders, all minimising the SAH cost C = 1 + (A_L N_L + A_R N_R) / A
+ * per split (leaf cost N):
+ *   ET_BVH_GPU    32 centroid bins per axis, on the device, level by level (fast);
+ *   ET_BVH_HOST   the same binned heuristic on the host;
+ *   ET_BVH_SWEEP  every split of the centroid order on each axis, on the host
+ *                 (O(n log n); slower to build, fewer traversal steps).
+ * A requested build whose tree is deeper than the traversal stack's 64 levels
+ * (or a GPU build that fails) is replaced by the host binned build. */
+enum { ET_BVH_GPU = 0, ET_BVH_HOST = 1, ET_BVH_SWEEP = 2 };
+#define ET_BVH_DEFAULT ET_BVH_SWEEP
+/* et_build_scene with an explicit builder.  Errors as et_build_scene, and
+ * ET_ERR_ARG for an unknown builder. */
+int et_build_scene_with(const float* tris, const uint32_t* tri_mat, int64_t n_tris,
+                        const et_material* mats, int32_t n_mats,
+                        const et_quad_light* lights, int32_t n_lights, float env,
+                        int32_t builder, et_scene** out, void* stream);
 void et_scene_free(et_scene* scene);
-/* Which builder produced the hierarchy: ET_BVH_GPU (binned SAH on the device,
- * the default) or ET_BVH_HOST (the same heuristic on the host, used when the
- * device tree would be deeper than the traversal stack's 64 levels). */
-enum { ET_BVH_GPU = 0, ET_BVH_HOST = 1 };
+/* Which builder produced the hierarchy (ET_BVH_*). */
 int et_scene_builder(const et_scene* scene);
 /* Triangle count (including the lights' triangles), BVH node count and its SAH
  * cost (C_trav = C_isect = 1, normalised by the root's surface area). */

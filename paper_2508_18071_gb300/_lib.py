@@ -16,7 +16,7 @@ ET_LOG_EPS, ET_LOG_PAPER = 0, 1
 ET_F32, ET_BF16, ET_FP8 = 0, 1, 2
 ET_NET_STACK, ET_NET_RESIDUAL = 0, 1
 ET_RENDER_WAVEFRONT, ET_RENDER_MEGAKERNEL = 0, 1
-ET_BVH_GPU, ET_BVH_HOST = 0, 1
+ET_BVH_GPU, ET_BVH_HOST, ET_BVH_SWEEP = 0, 1, 2
 
 
 class et_material(C.Structure):
@@ -54,6 +54,7 @@ EVENT_BYTES = 12
 P, i32, i64, u64, f32, f64 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64, C.c_float, C.c_double
 SIGNATURES = {
     "et_build_scene": (i32, [P, P, i64, P, i32, P, i32, f32, P, P]),
+    "et_build_scene_with": (i32, [P, P, i64, P, i32, P, i32, f32, i32, P, P]),
     "et_scene_free": (None, [P]),
     "et_scene_info": (i32, [P, P, P, P]),
     "et_scene_builder": (i32, [P]),

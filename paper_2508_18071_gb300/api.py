@@ -31,9 +31,12 @@ def _ptr(t: Optional[torch.Tensor]):
 
 # ----------------------------------------------------------------------- scene
 class Scene:
-    """et_build_scene: geometry + BVH on the device (see inputs.py for the dict layout)."""
+    """et_build_scene: geometry + BVH on the device (see inputs.py for the dict layout).
+    builder: None (the library's default), "gpu", "host" or "sweep" (et_build_scene_with)."""
 
-    def __init__(self, scene: dict, stream=None):
+    BUILDERS = {"gpu": L.ET_BVH_GPU, "host": L.ET_BVH_HOST, "sweep": L.ET_BVH_SWEEP}
+
+    def __init__(self, scene: dict, stream=None, builder=None):
         lib = L.load()
         tris = np.ascontiguousarray(scene["tris"], np.float32).reshape(-1, 9)
         tri_mat = np.ascontiguousarray(scene["tri_mat"], np.uint32).reshape(-1)
@@ -51,9 +54,15 @@ class Scene:
             cl[i].e2[:] = [float(v) for v in q[6:9]]
             cl[i].radiance[:] = [float(v) for v in q[9:12]]
         h = C.c_void_p()
-        st = lib.et_build_scene(tris.ctypes.data_as(C.c_void_p), tri_mat.ctypes.data_as(C.c_void_p),
-                                tris.shape[0], cm, len(mats), cl, len(lights),
-                                float(scene.get("env", 0.0)), C.byref(h), _stream(stream))
+        if builder is None:
+            st = lib.et_build_scene(tris.ctypes.data_as(C.c_void_p), tri_mat.ctypes.data_as(C.c_void_p),
+                                    tris.shape[0], cm, len(mats), cl, len(lights),
+                                    float(scene.get("env", 0.0)), C.byref(h), _stream(stream))
+        else:
+            st = lib.et_build_scene_with(tris.ctypes.data_as(C.c_void_p),
+                                         tri_mat.ctypes.data_as(C.c_void_p), tris.shape[0], cm,
+                                         len(mats), cl, len(lights), float(scene.get("env", 0.0)),
+                                         self.BUILDERS[builder], C.byref(h), _stream(stream))
         L.check("et_build_scene", st)
         self._h = h
 
@@ -64,7 +73,8 @@ class Scene:
     def info(self):
         n, nn, sah = C.c_int64(), C.c_int64(), C.c_double()
         L.check("et_scene_info", L.load().et_scene_info(self._h, C.byref(n), C.byref(nn), C.byref(sah)))
-        builder = "gpu" if L.load().et_scene_builder(self._h) == L.ET_BVH_GPU else "host"
+        b = L.load().et_scene_builder(self._h)
+        builder = {v: k for k, v in self.BUILDERS.items()}[b]
         return {"n_tris": n.value, "n_nodes": nn.value, "sah_cost": sah.value, "builder": builder}
 
     def free(self):
