@@ -291,6 +291,21 @@ const char* et_status_str(int status);
  * devices, all calls); a monotone counter for instrumentation. */
 uint64_t et_kernel_launches(void);
 
+/* Failure detection.  The tensor-core EvSNet kernel waits on its MMAs with a
+ * bounded number of mbarrier polls (default 2^22).  When a wait runs out the
+ * kernel sets bit 62 of *n_events (which the caller reports as ET_ERR_TIMEOUT),
+ * leaves the membrane state of the call untouched, waits once more with the
+ * default bound for the MMAs still in flight, frees its tensor memory and
+ * returns; the context stays usable.  The call's previous-frame buffer and
+ * `initialized` flag are still updated (the host does not see the timeout until
+ * it reads the count): restore the state from a copy before retrying.
+ * et_set_wait_budget(polls) sets the first bound for launches made afterwards in
+ * this process: polls >= 0 sets it (0 gives up at once and forces the timeout
+ * path, for testing the detection), polls < 0 restores the default.  (A poll
+ * is one mbarrier.try_wait, which may itself suspend the thread for a while.)
+ * Not thread-safe against concurrent launches. */
+void et_set_wait_budget(int64_t polls);
+
 #ifdef __cplusplus
 }
 #endif

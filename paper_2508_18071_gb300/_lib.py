@@ -72,6 +72,7 @@ SIGNATURES = {
     "et_event_matches": (i32, [P, i64, P, i64, i32, P]),
     "et_status_str": (C.c_char_p, [i32]),
     "et_kernel_launches": (u64, []),
+    "et_set_wait_budget": (None, [i64]),
 }
 
 _lib = None

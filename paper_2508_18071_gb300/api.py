@@ -252,6 +252,26 @@ class EvsStateDev:
         return L.et_evsnet_state(self.V.data_ptr(), self.hist.data_ptr() if self._has_hist else None,
                                  self.last_l.data_ptr(), self.H, self.W, self.initialized)
 
+    def save(self, path: str):
+        """Checkpoint: the state is plain buffers (V, temporal history, previous
+        log frame) and the initialized flag; a clip resumed from it continues
+        bit for bit."""
+        np.savez(path, V=self.V.cpu().numpy(), hist=self.hist.cpu().numpy(),
+                 last_l=self.last_l.cpu().numpy(), H=self.H, W=self.W,
+                 initialized=self.initialized)
+
+    @staticmethod
+    def load(path: str, net: "EvsNetDev") -> "EvsStateDev":
+        z = np.load(path)
+        st = EvsStateDev(net, int(z["H"]), int(z["W"]))
+        if z["hist"].shape != tuple(st.hist.shape):
+            raise ValueError("state checkpoint does not match the network's history size")
+        st.V.copy_(torch.as_tensor(z["V"]))
+        st.hist.copy_(torch.as_tensor(z["hist"]))
+        st.last_l.copy_(torch.as_tensor(z["last_l"]))
+        st.initialized = int(z["initialized"])
+        return st
+
 
 def evsnet_forward(logl: torch.Tensor, net: EvsNetDev, state: EvsStateDev, t0=0,
                    buf: Optional[EventBuffer] = None, want_I=False, want_spikes=False, stream=None):

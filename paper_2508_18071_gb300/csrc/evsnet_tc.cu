@@ -33,12 +33,14 @@
 #include "tc_ptx.cuh"
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
+#include <algorithm>
 
 namespace {
 
 constexpr int TW = 32, TH = 16;
 constexpr int kThreads = 128;
 constexpr uint32_t kWaitIters = 1u << 22;
+int64_t g_wait_budget = -1;          // < 0: kWaitIters
 constexpr unsigned long long kTimeoutBit = 1ull << 62;
 constexpr float kE4M3Max = 448.0f;
 
@@ -51,6 +53,7 @@ struct TcParams {
   int off_act1, off_wB, off_f32, off_cur, off_prev, off_V;  // smem byte offsets
   int nb1;                              // M blocks of layer 1 (the widest)
   uint32_t tmem_cols;
+  uint32_t wait_iters;                  // bound of the per-layer MMA waits
 };
 
 // smallest power of two >= x / 448 (1 for x == 0): the E4M3 scale of a tensor
@@ -279,7 +282,7 @@ evsnet_tc_kernel(TcParams P, const float* __restrict__ logl, const float* __rest
         }
         umma_commit(&mma_bar);
       }
-      const bool ok = mbar_wait(&mma_bar, phase, kWaitIters);
+      const bool ok = mbar_wait(&mma_bar, phase, P.wait_iters);
       phase ^= 1;
       if (!ok) {
         if (lane == 0) atomicOr(n_events, kTimeoutBit);
@@ -399,6 +402,7 @@ int launch(const float* logl, int32_t F, const et_evsnet_weights* net, et_evsnet
   while (cols < (uint32_t)(P.nb1 * CP)) cols <<= 1;
   if (cols > 512) return ET_ERR_UNIMPLEMENTED;
   P.tmem_cols = cols;
+  P.wait_iters = g_wait_budget < 0 ? kWaitIters : (uint32_t)std::min<int64_t>(g_wait_budget, 0xFFFFFFFFll);
   int dev = 0, max_smem = 0;
   ET_CHECK_CUDA(cudaGetDevice(&dev));
   ET_CHECK_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
@@ -413,6 +417,8 @@ int launch(const float* logl, int32_t F, const et_evsnet_weights* net, et_evsnet
 }
 
 }  // namespace
+
+extern "C" void et_set_wait_budget(int64_t polls) { g_wait_budget = polls; }
 
 int et_evsnet_forward_tc(const float* logl, int32_t F, const et_evsnet_weights* net,
                          et_evsnet_state* st, int32_t t0, et_event* events, int64_t cap,

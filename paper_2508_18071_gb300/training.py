@@ -184,6 +184,29 @@ class Trainer:
         adam_step(self.b, self.gb, self.mb, self.vb, self.t, self.lr)
         return loss
 
+    def save(self, path: str):
+        """Checkpoint: FP32 weights, Adam moments, step count and hyper-parameters."""
+        m = self.meta
+        np.savez(path, w=self.w.cpu().numpy(), b=self.b.cpu().numpy(), mw=self.mw.cpu().numpy(),
+                 vw=self.vw.cpu().numpy(), mb=self.mb.cpu().numpy(), vb=self.vb.cpu().numpy(),
+                 t=self.t, lr=self.lr, lam=self.lam, alpha=self.alpha, ckpt=self.ckpt,
+                 meta=np.array([m.kind, m.n_layers, m.C, m.kt, m.ks]),
+                 lif=np.array([m.beta, m.vth, m.reset], np.float64))
+
+    @staticmethod
+    def load(path: str) -> "Trainer":
+        z = np.load(path)
+        kind, n_layers, C, kt, ks = (int(v) for v in z["meta"])
+        beta, vth, reset = (float(v) for v in z["lif"])
+        net = {"kind": kind, "n_layers": n_layers, "C": C, "kt": kt, "ks": ks, "beta": beta,
+               "vth": vth, "reset": reset, "w": z["w"], "b": z["b"]}
+        T = Trainer(net, lr=float(z["lr"]), lam=float(z["lam"]), alpha=float(z["alpha"]),
+                    ckpt_every=int(z["ckpt"]))
+        for k in ("mw", "vw", "mb", "vb"):
+            getattr(T, k).copy_(torch.as_tensor(z[k]))
+        T.t = int(z["t"])
+        return T
+
     def net_dict(self) -> dict:
         m = self.meta
         return {"kind": m.kind, "n_layers": m.n_layers, "C": m.C, "kt": m.kt, "ks": m.ks,

@@ -89,3 +89,38 @@ def test_sharded_equals_unsharded(orc, mode):
         ref, _, _ = orc.evsnet_forward(lf, net, orc.EvsState.new(net, 30, 26))
     assert len(ref) > 100
     np.testing.assert_array_equal(got, sharding.sort_events(ref))
+
+
+def _dying_worker(rank, world, port, q):
+    """Rank 1 fails between steps (before the event gather, with nothing in
+    flight); rank 0 must learn of it from its next collective."""
+    import datetime
+    import time
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world,
+                            timeout=datetime.timedelta(seconds=20))
+    if rank == 1:
+        os._exit(3)
+    t0 = time.time()
+    try:
+        sharding.gather_events(np.zeros((5, 4), np.int32))
+        q.put(("not detected", time.time() - t0))
+    except Exception as e:  # noqa: BLE001 - any collective error is the detection
+        q.put(("detected", time.time() - t0, type(e).__name__))
+
+
+def test_failed_rank_is_detected_by_the_next_collective():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_dying_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = q.get(timeout=120)
+    for p in procs:
+        p.join(60)
+    assert out[0] == "detected", out
+    assert out[1] < 60.0, out
+    assert procs[1].exitcode == 3
