@@ -24,7 +24,7 @@
 namespace {
 
 constexpr unsigned FULL = 0xFFFFFFFFu;
-constexpr int kLeafBatch = 16;       // lanes waiting at leaves that end a node phase
+constexpr int kLeafBatch = 24;       // lanes waiting at leaves that end a node phase
 constexpr int64_t kPathCap = 8 << 20;
 
 enum { C_NRAY0 = 0, C_NRAY1 = 1, C_NSH = 2, C_FETCH = 3, C_FETCH_SH = 4, C_N = 8 };
