@@ -63,6 +63,11 @@ def lib():
                                          C.c_double, C.c_double, P, P, i32, P, P, P, P, P, i64,
                                          P, P, i32]
         L.orc_evsnet_forward.restype = i64
+        L.orc_sensor_events.argtypes = [P, i32, i32, i32, C.c_double, C.c_double, C.c_double,
+                                        C.c_double, C.c_double, C.c_double, C.c_uint64, i32, P,
+                                        P, P, i64]
+        L.orc_sensor_events.restype = i64
+        L.orc_sensor_thresholds.argtypes = [i64, C.c_double, C.c_double, C.c_uint64, P]
         L.orc_event_matches.argtypes = [P, i64, P, i64, i32]
         L.orc_event_matches.restype = i64
         L.orc_bsdf_eval.argtypes = [P, P, P, i64, P, P]
@@ -245,6 +250,63 @@ def threshold_events(logl_frames, C_thr, state: ThresholdState, t0=0):
     state.ref[:] = ref
     state.initialized = ini.value
     return ev[:n].copy()
+
+
+# ------------------------------------------------------------ sensor model
+@dataclass
+class SensorParams:
+    """Event-sensor model (oracle/sensor.c).  Float parameters are float32
+    quantities (the library's interface), widened to FP64."""
+    C: float = 0.2
+    sigma_C: float = 0.0          # relative threshold mismatch (std)
+    refractory_us: float = 0.0
+    leak_hz: float = 0.0
+    shot_hz: float = 0.0
+    frame_hz: float = 1000.0
+    seed: int = 0
+
+    def f64(self):
+        return tuple(float(np.float32(v)) for v in (self.C, self.sigma_C, self.refractory_us,
+                                                     self.leak_hz, self.shot_hz, self.frame_hz))
+
+
+@dataclass
+class SensorState:
+    s: np.ndarray                 # [H*W][3]: reference, last event time, previous log intensity
+    initialized: int = 0
+
+    @staticmethod
+    def new(H, W):
+        return SensorState(np.zeros((H * W, 3), np.float64), 0)
+
+
+def sensor_events(logl_frames, prm: SensorParams, state: SensorState, t0=0):
+    """Sensor-model events from float32 log frames [F,H,W] -> int64 [n,4]
+    (x, y, t in microseconds, p), in pixel order."""
+    lf = _c(logl_frames, np.float32)
+    F, H, W = lf.shape
+    C_, sg, tr, lk, sh, fr = prm.f64()
+    cap = 1 << 16
+    while True:
+        st = state.s.copy()
+        ini = C.c_int(state.initialized)
+        ev = np.empty((cap, 4), np.int64)
+        n = lib().orc_sensor_events(_p(lf), F, H, W, C_, sg, tr, lk, sh, fr, int(prm.seed), t0,
+                                    _p(st), C.byref(ini), _p(ev), cap)
+        if n <= cap:
+            break
+        cap = int(n)
+    state.s[:] = st
+    state.initialized = ini.value
+    return ev[:n].copy()
+
+
+def sensor_thresholds(npix, prm: SensorParams):
+    """Per-pixel (C_on, C_off) [npix, 2] of the mismatch model."""
+    C_, sg = prm.f64()[:2]
+    out = np.empty((npix, 2), np.float64)
+    lib().orc_sensor_thresholds(npix, C_, sg, int(prm.seed), _p(out))
+    return out
 
 
 # --------------------------------------------------------------------- EvSNet

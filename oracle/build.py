@@ -10,7 +10,7 @@ import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SOURCES = ["philox.c", "trace.c", "events.c"]
+SOURCES = ["philox.c", "trace.c", "events.c", "sensor.c"]
 LIB = os.path.join(HERE, "liboracle.so")
 
 

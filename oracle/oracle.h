@@ -25,6 +25,7 @@ extern "C" {
 
 /* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), n independent blocks. */
 void orc_philox4x32_10(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t n);
+void orc_philox_block(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 
 typedef struct orc_scene orc_scene;
 
@@ -81,6 +82,14 @@ void orc_bsdf_eval(const double* mat5, const double* wo, const double* wi, int64
 void orc_bsdf_sample(const double* mat5, const double* wo, const double* u, int64_t n,
                      double* wi, double* weight, double* pdf, int32_t* ok);
 void orc_bvh_export(const orc_scene* s, double* bounds, int32_t* links, int32_t* perm);
+
+/* event-sensor model (sensor.c): state [H*W][3] = (r, t_last, previous log
+   intensity); events [n][4] int64 {x, y, t in microseconds, p} */
+int64_t orc_sensor_events(const float* logl, int F, int H, int W, double C, double sigma,
+                          double refractory_us, double leak_hz, double shot_hz, double frame_hz,
+                          uint64_t seed, int t0, double* state, int* initialized,
+                          int64_t* events, int64_t cap);
+void orc_sensor_thresholds(int64_t npix, double C, double sigma, uint64_t seed, double* out);
 
 /* number of matched pairs between two event lists [n][4] {x,y,t,p} */
 int64_t orc_event_matches(const int32_t* A, int64_t na, const int32_t* B, int64_t nb, int delta);
