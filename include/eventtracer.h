@@ -153,6 +153,53 @@ int et_threshold_events(const float* logl, int32_t F, int32_t H, int32_t W, floa
                         double* ref, int32_t initialized, et_event* events, int64_t cap,
                         int64_t* n_events, void* stream);
 
+/* --------------------------------------------------------------- sensor model
+ * Contrast-threshold events with sub-frame timestamps and the sensor
+ * non-idealities the paper names beside internal-state bias and saturation
+ * (Sec. 3.1: threshold mismatch, leak events, shot noise; the reset period
+ * behind the saturation effect).  The paper gives no formulas; this model:
+ *   - frame k is at time k (frames); between frames the log intensity is
+ *     linear in time;
+ *   - per-pixel thresholds C_on/off = C max(0.01, 1 + sigma_C z), z = (u0 + u1 +
+ *     u2 + u3 - 2) sqrt 3 (unit variance), u = Philox4x32-10(key = seed,
+ *     counter = (pixel y W + x, 0xFFFFFFFF, 0 ON / 1 OFF, 0x53454E53)) as
+ *     (u32 >> 8) 2^-24;
+ *   - per step k-1 -> k: the reference drops by C_on leak_hz / frame_hz (leak);
+ *     then repeatedly the pixel fires at the earliest t >= max(k - 1, t_last +
+ *     refractory) in the step where l(t) - r >= C_on (ON) or r - l(t) >= C_off
+ *     (OFF), moving r by +-C_on/off and setting t_last = t; finally, with
+ *     probability shot_hz / frame_hz, one shot-noise event at t = k - 1 + v of
+ *     polarity + if w < 1/2 (u, v, w from counter (pixel, k, 2, 0x53454E53));
+ *     shot events leave the state alone;
+ *   - event records carry t = floor(time * 1e6 / frame_hz) in microseconds.
+ * With sigma_C = 0 and no refractory period, leak or shot noise each step emits
+ * the contrast-threshold generator's floor(|l_k - r| / C) events.  At most 1024
+ * threshold events per pixel and step (a bound on the work): further crossings
+ * of that step are dropped and the reference stops there.  Decisions
+ * are FP64 with explicit rounding: bit-reproducible.  Float parameters are
+ * widened to FP64 as given. */
+typedef struct {
+  float C;              /* nominal threshold (log units), > 0 */
+  float sigma_C;        /* relative per-pixel threshold spread (std), >= 0 */
+  float refractory_us;  /* >= 0 */
+  float leak_hz;        /* leak-event rate of a static pixel, >= 0 */
+  float shot_hz;        /* shot-noise events per pixel and second, <= frame_hz */
+  float frame_hz;       /* frame rate F_evt, > 0 (1000 for 1 kHz) */
+  uint64_t seed;        /* Philox key for the mismatch and the shot noise */
+} et_sensor_params;
+
+/* Events of F log frames (device float [F][H][W]; frame f is frame t0 + f of
+ * the clip).  state: device double [H*W][3] = (reference, time of the last
+ * event, previous log intensity); with initialized = 0 the first frame only
+ * sets it (t0 >= 0), else the call continues the clip (t0 >= 1).  Events as
+ * et_threshold_events, with t in microseconds.
+ * Errors: ET_ERR_ARG (sizes, parameters outside the ranges above, times that
+ * overflow 32 bits), ET_ERR_CUDA. */
+int et_sensor_events(const float* logl, int32_t F, int32_t H, int32_t W,
+                     const et_sensor_params* params, int32_t t0, double* state,
+                     int32_t initialized, et_event* events, int64_t cap, int64_t* n_events,
+                     void* stream);
+
 /* --------------------------------------------------------------------- EvSNet
  * Weights (device, FP32, packed): conv layers 0..n_layers-1 in order, each
  * W[C][Cin][kt][ks][ks] with Cin = 1 for layer 0 and C otherwise, then the

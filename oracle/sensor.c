@@ -25,13 +25,16 @@
  *                      not touch the state
  *   output          (x, y, floor(t * 1e6 / frame_hz) microseconds, polarity)
  * With sigma = 0, no refractory period, no leak and no shot noise every step
- * emits floor(|l_k - r| / C) events, as the contrast-threshold generator.
+ * emits floor(|l_k - r| / C) events, as the contrast-threshold generator (up
+ * to 1024 per pixel and step: a bound on the work, further crossings of that
+ * step are dropped).
  */
 #include <math.h>
 #include <stdint.h>
 #include "oracle.h"
 
 #define SENSOR_TAG 0x53454E53u   /* "SENS" */
+#define MAX_PER_STEP 1024         /* events of one pixel in one step; further crossings are dropped */
 
 static double u01(uint32_t x) { return (double)(x >> 8) * (1.0 / 16777216.0); }
 
@@ -93,7 +96,8 @@ int64_t orc_sensor_events(const float* logl, int F, int H, int W, double C, doub
       const double la = l_prev;
       const double lb = (double)logl[(int64_t)f * npix + q];
       r = r - c_on * leak;
-      for (;;) {
+      for (int n_step = 0;; ++n_step) {
+        if (n_step >= MAX_PER_STEP) break;
         const double lo = t_last + t_ref > a ? t_last + t_ref : a;
         if (lo > b) break;
         const double l_lo = lerp_at(la, lb, a, lo);

@@ -32,6 +32,12 @@ class et_camera(C.Structure):
     _fields_ = [("pos", C.c_float * 3), ("rot", C.c_float * 9), ("vfov_deg", C.c_float)]
 
 
+class et_sensor_params(C.Structure):
+    _fields_ = [("C", C.c_float), ("sigma_C", C.c_float), ("refractory_us", C.c_float),
+                ("leak_hz", C.c_float), ("shot_hz", C.c_float), ("frame_hz", C.c_float),
+                ("seed", C.c_uint64)]
+
+
 class et_evsnet_weights(C.Structure):
     _fields_ = [("kind", C.c_int32), ("n_layers", C.c_int32), ("C", C.c_int32),
                 ("kt", C.c_int32), ("ks", C.c_int32), ("beta", C.c_float), ("vth", C.c_float),
@@ -72,6 +78,7 @@ SIGNATURES = {
     "et_event_matches": (i32, [P, i64, P, i64, i32, P]),
     "et_status_str": (C.c_char_p, [i32]),
     "et_kernel_launches": (u64, []),
+    "et_sensor_events": (i32, [P, i32, i32, i32, P, i32, P, i32, P, i64, P, P]),
     "et_set_wait_budget": (None, [i64]),
 }
 

@@ -207,6 +207,64 @@ def event_f1(pred: np.ndarray, ref: np.ndarray, delta: int) -> float:
     return 2.0 * m.value / (na + nb)
 
 
+# ------------------------------------------------------------ sensor model
+@dataclass
+class SensorParams:
+    """et_sensor_params: threshold C, relative mismatch sigma_C, refractory
+    period (us), leak and shot-noise rates (Hz), frame rate (Hz), seed."""
+    C: float = 0.2
+    sigma_C: float = 0.0
+    refractory_us: float = 0.0
+    leak_hz: float = 0.0
+    shot_hz: float = 0.0
+    frame_hz: float = 1000.0
+    seed: int = 0
+
+    def c_struct(self):
+        return L.et_sensor_params(self.C, self.sigma_C, self.refractory_us, self.leak_hz,
+                                  self.shot_hz, self.frame_hz, int(self.seed))
+
+
+class SensorStateDev:
+    """Device state of the sensor model: double [H*W][3] (reference, time of the
+    last event, previous log intensity)."""
+
+    def __init__(self, H, W):
+        self.H, self.W = H, W
+        self.s = torch.zeros((H * W, 3), dtype=torch.float64, device="cuda")
+        self.initialized = 0
+
+
+def sensor_events(logl: torch.Tensor, prm: SensorParams, state: SensorStateDev, t0=0,
+                  buf: Optional[EventBuffer] = None, stream=None, grow: bool = True) -> EventBuffer:
+    """et_sensor_events on device log frames [F,H,W]; events carry t in
+    microseconds.  With grow=True and no caller buffer an overflowing call is
+    repeated once with a buffer of the reported size (state restored first)."""
+    F, H, W = logl.shape
+    own = buf is None
+    if own:
+        buf = EventBuffer(max(1 << 16, 2 * F * H * W))
+    saved = state.s.clone() if (own and grow) else None
+    cp = prm.c_struct()
+    ini0 = state.initialized
+
+    def call(b):
+        st = L.load().et_sensor_events(_ptr(logl), F, H, W, C.byref(cp), int(t0), _ptr(state.s),
+                                       int(ini0), _ptr(b.raw), b.cap, _ptr(b.count), _stream(stream))
+        L.check("et_sensor_events", st)
+
+    call(buf)
+    if saved is not None:
+        n = buf.n()
+        if n > buf.cap:
+            state.s.copy_(saved)
+            buf = EventBuffer(n)
+            call(buf)
+    if F > 0:
+        state.initialized = 1
+    return buf
+
+
 # ------------------------------------------------------------------ EvSNet
 @dataclass
 class EvsNetDev:

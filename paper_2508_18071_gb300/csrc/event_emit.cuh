@@ -22,12 +22,11 @@ __device__ __forceinline__ void emit_events_warp(et_event* events, int64_t cap,
   base = __shfl_sync(0xFFFFFFFFu, base, 31);
   const unsigned long long start = base + (incl - n);
   uint32_t* out = reinterpret_cast<uint32_t*>(events);
-  for (uint32_t i = 0; i < n; ++i) {
+  // slots at or beyond cap are counted only: the loop stops there
+  for (uint32_t i = 0; i < n && start + i < (unsigned long long)cap; ++i) {
     const unsigned long long slot = start + i;
-    if (slot < (unsigned long long)cap) {
-      out[3 * slot] = x | (y << 16);
-      out[3 * slot + 1] = t;
-      out[3 * slot + 2] = (uint32_t)(uint8_t)(int8_t)p;
-    }
+    out[3 * slot] = x | (y << 16);
+    out[3 * slot + 1] = t;
+    out[3 * slot + 2] = (uint32_t)(uint8_t)(int8_t)p;
   }
 }
