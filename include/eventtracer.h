@@ -253,8 +253,10 @@ int et_evsnet_forward(const float* logl, int32_t F, const et_evsnet_weights* net
                       int64_t* n_events, float* I_out, int8_t* spikes, void* stream);
 
 /* ------------------------------------------------------------------ training
- * The learned form: EvSNet (plain stack of 3x3 convolutions, <= 16 channels,
- * FP32 weights) trained on B clips of K steps.  Inputs are log frames
+ * The learned form: EvSNet with FP32 weights, <= 16 channels, trained on B clips
+ * of K steps, in either of two forms: the spatial one (plain stack of 3x3
+ * convolutions, kt = 1) or the paper's pixel-wise temporal one (ks = 1, causal
+ * kernel kt <= 9, plain stack or residual blocks, Eq. 5).  Inputs are log frames
  * logl [B][K+1][H][W] (device, FP32; step k uses X = l_{k+1} - l_k, Eq. 1) and
  * targets E [B][K][H][W] (device, FP32 signed event counts per step).
  * Spikes follow Eq. 3 read as S_on = Theta(V' - Vth), S_off = Theta(-V' - Vth);
@@ -265,16 +267,17 @@ int et_evsnet_forward(const float* logl, int32_t F, const et_evsnet_weights* net
 typedef struct { int32_t B, K, H, W, ckpt_every; } et_train_shape;
 
 /* Bytes of the caller-allocated device workspace the two calls below need:
- * the activations of one segment plus its gradients (about
- * (2 n_layers + 2) C B ckpt_every H W floats). */
+ * spatial form: the activations of one segment plus its gradients (about
+ * (2 n_layers + 2) C B ckpt_every H W floats); temporal form: the activations
+ * of the whole clip (about (n_layers + 3) C B K H W floats). */
 int et_train_workspace_bytes(const et_evsnet_weights* net, const et_train_shape* shape,
                              size_t* bytes);
 
 /* Forward over the batch.  Outputs (device): spikes int8 [B][K][H][W] (S_on - S_off),
  * optional S_on / S_off float [B][K][H][W] (both or neither), V_ckpt float
  * [B][ceil(K / ckpt_every)][H][W], optional I_out float [B][K][H][W].
- * Errors: ET_ERR_ARG, ET_ERR_UNIMPLEMENTED (form other than a 3x3 stack, C > 16,
- * dtype other than ET_F32, ckpt_every > 32), ET_ERR_CUDA. */
+ * Errors: ET_ERR_ARG, ET_ERR_UNIMPLEMENTED (a form other than the two above,
+ * C > 16, dtype other than ET_F32, ckpt_every > 32), ET_ERR_CUDA. */
 int et_evsnet_train_forward(const float* logl, const et_train_shape* shape,
                             const et_evsnet_weights* net, int8_t* spikes, float* S_on,
                             float* S_off, float* V_ckpt, float* I_out, void* workspace,

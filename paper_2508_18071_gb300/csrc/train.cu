@@ -1,5 +1,6 @@
 // Training of the spatial EvSNet (stack of 3x3 convolutions + projection +
-// BiLIF) on the GPU: forward with membrane checkpoints, the paper's loss
+// BiLIF; the paper's temporal form is in train_temporal.cu and is dispatched
+// from the entry points below) on the GPU: forward with membrane checkpoints, the paper's loss
 // (Eq. 7-11) with its gradient, surrogate-gradient BPTT (Eq. 4), and Adam.
 //
 // Layout: B clips of K steps of H x W pixels.  Time is processed in segments of
@@ -426,9 +427,10 @@ bool layout(const et_evsnet_weights* net, const et_train_shape* sh, char* base, 
 int check(const et_evsnet_weights* net, const et_train_shape* sh) {
   if (!net || !sh || !net->w || !net->b) return ET_ERR_ARG;
   if (sh->B < 1 || sh->K < 1 || sh->H < 1 || sh->W < 1 || sh->ckpt_every < 1) return ET_ERR_ARG;
-  if (net->kind != ET_NET_STACK || net->ks != 3 || net->kt != 1 || net->C > kMaxC ||
-      net->n_layers < 1 || net->n_layers > kMaxLayers || net->dtype != ET_F32)
+  if (net->n_layers < 1 || net->n_layers > kMaxLayers || net->C < 1 || net->dtype != ET_F32)
     return ET_ERR_UNIMPLEMENTED;
+  const bool spatial = net->kind == ET_NET_STACK && net->ks == 3 && net->kt == 1 && net->C <= kMaxC;
+  if (!spatial && !et_train_is_temporal(net)) return ET_ERR_UNIMPLEMENTED;
   if (sh->ckpt_every > kMaxSeg) return ET_ERR_UNIMPLEMENTED;
   return ET_OK;
 }
@@ -462,6 +464,10 @@ extern "C" int et_train_workspace_bytes(const et_evsnet_weights* net, const et_t
   const int rc = check(net, sh);
   if (rc != ET_OK) return rc;
   if (!bytes) return ET_ERR_ARG;
+  if (et_train_is_temporal(net)) {
+    *bytes = et_train_temporal_bytes(net, sh);
+    return ET_OK;
+  }
   Workspace ws{};
   layout(net, sh, nullptr, &ws);
   *bytes = ws.bytes;
@@ -476,6 +482,11 @@ extern "C" int et_evsnet_train_forward(const float* logl, const et_train_shape* 
   if (rc != ET_OK) return rc;
   if (!logl || !spikes || !V_ckpt || !workspace || ((S_on == nullptr) != (S_off == nullptr)))
     return ET_ERR_ARG;
+  if (et_train_is_temporal(net)) {
+    if (ws_bytes < et_train_temporal_bytes(net, sh)) return ET_ERR_ARG;
+    return et_train_temporal_forward(logl, sh, net, spikes, S_on, S_off, V_ckpt, I_out, workspace,
+                                     (cudaStream_t)stream_);
+  }
   Workspace ws{};
   layout(net, sh, nullptr, &ws);
   if (ws_bytes < ws.bytes) return ET_ERR_ARG;
@@ -519,6 +530,11 @@ extern "C" int et_evsnet_train_backward(const float* logl, const et_train_shape*
   int rc = check(net, sh);
   if (rc != ET_OK) return rc;
   if (!logl || !V_ckpt || !dS_on || !dS_off || !grad_w || !grad_b || !workspace) return ET_ERR_ARG;
+  if (et_train_is_temporal(net)) {
+    if (ws_bytes < et_train_temporal_bytes(net, sh)) return ET_ERR_ARG;
+    return et_train_temporal_backward(logl, sh, net, V_ckpt, dS_on, dS_off, alpha, grad_w, grad_b,
+                                      workspace, (cudaStream_t)stream_);
+  }
   Workspace ws{};
   layout(net, sh, nullptr, &ws);
   if (ws_bytes < ws.bytes) return ET_ERR_ARG;

@@ -3,3 +3,19 @@
 #include "../../include/eventtracer.h"
 
 constexpr int kMaxSeg = 32;   // longest BPTT segment (membrane checkpoint interval)
+
+#include <cuda_runtime.h>
+
+// The paper's pixel-wise temporal form (1x1 spatial extent, causal kernel kt,
+// plain stack or residual blocks), trained with whole-clip activations
+// (train_temporal.cu).
+bool et_train_is_temporal(const et_evsnet_weights* net);
+size_t et_train_temporal_bytes(const et_evsnet_weights* net, const et_train_shape* sh);
+int et_train_temporal_forward(const float* logl, const et_train_shape* sh,
+                              const et_evsnet_weights* net, int8_t* spikes, float* S_on,
+                              float* S_off, float* V_ckpt, float* I_out, void* workspace,
+                              cudaStream_t st);
+int et_train_temporal_backward(const float* logl, const et_train_shape* sh,
+                               const et_evsnet_weights* net, const float* V_ckpt,
+                               const float* dS_on, const float* dS_off, float alpha,
+                               float* grad_w, float* grad_b, void* workspace, cudaStream_t st);

@@ -296,6 +296,34 @@ def test_smooth_surrogate_gradient_matches_finite_differences(orc):
         assert abs(fd - gb[idx]) <= 1e-5 * max(1.0, abs(fd)) + 1e-8
 
 
+def test_smooth_surrogate_gradient_temporal_residual_form(orc):
+    """P10 for the paper's temporal form (causal kernel 4 along time, one
+    residual block): the autograd gradient matches central differences."""
+    d = inputs.random_evsnet(1, 3, 3, 4, 1, seed=5, vth=0.3, beta=0.9, std=0.3)
+    net = _net(orc, d)
+    rng = np.random.default_rng(5)
+    X = rng.normal(0, 0.3, (2, 14, 3, 4))
+    E = rng.choice([-1, 0, 0, 0, 1, 2], X.shape).astype(float)
+    _, gw, gb = orc.torch_grads(X, E, net, smooth=True)
+    h = 1e-6
+    for idx in list(rng.choice(len(net.w), 10, replace=False)) + [len(net.w) - 1]:
+        wp, wm = net.w.copy(), net.w.copy()
+        wp[idx] += h
+        wm[idx] -= h
+        lp = orc.torch_grads(X, E, orc.EvsNet(**{**net.__dict__, "w": wp}), smooth=True)[0]
+        lm = orc.torch_grads(X, E, orc.EvsNet(**{**net.__dict__, "w": wm}), smooth=True)[0]
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - gw[idx]) <= 1e-5 * max(1.0, abs(fd)) + 1e-8, (idx, fd, gw[idx])
+    for idx in (0, len(net.b) // 2, len(net.b) - 1):
+        bp_, bm_ = net.b.copy(), net.b.copy()
+        bp_[idx] += h
+        bm_[idx] -= h
+        lp = orc.torch_grads(X, E, orc.EvsNet(**{**net.__dict__, "b": bp_}), smooth=True)[0]
+        lm = orc.torch_grads(X, E, orc.EvsNet(**{**net.__dict__, "b": bm_}), smooth=True)[0]
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - gb[idx]) <= 1e-5 * max(1.0, abs(fd)) + 1e-8
+
+
 def test_heaviside_forward_matches_c_oracle(orc):
     """The autograd forward (Theta spikes) emits the same spikes as the C oracle."""
     torch = pytest.importorskip("torch")
