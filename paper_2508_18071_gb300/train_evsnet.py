@@ -31,9 +31,14 @@ from . import api, inputs, training
 HERE = os.path.dirname(os.path.abspath(__file__))
 
 
-def identity_init(C=16, n_layers=4, vth=0.2, std=0.01, seed=0, beta=0.9):
-    """Identity 3x3 stack (channels 0/1 carry ReLU(+-X)) plus small noise."""
-    d = inputs.identity_evsnet(0, n_layers, C, 1, 3, vth=vth)
+def identity_init(C=16, n_layers=4, vth=0.2, std=0.01, seed=0, beta=0.9, form="spatial"):
+    """Identity network (channels 0/1 carry ReLU(+-X)) plus small noise: a stack
+    of 3x3 convolutions ("spatial"), or the paper's temporal form ("temporal":
+    kernel 7 along time, residual blocks, n_layers = 1 + 2M)."""
+    if form == "temporal":
+        d = inputs.identity_evsnet(1, n_layers, C, 7, 1, vth=vth)
+    else:
+        d = inputs.identity_evsnet(0, n_layers, C, 1, 3, vth=vth)
     rng = np.random.default_rng(seed)
     d["w"] = (d["w"] + rng.normal(0, std, d["w"].shape)).astype(np.float32)
     d["beta"] = float(beta)
@@ -93,7 +98,7 @@ def make_clips(scene: api.Scene, scene_kind, seeds, n_frames, size, spp_in, spp_
 
 def train(scene_kind="city", n_clips=32, n_frames=65, size=128, spp_in=2, spp_ref=256,
           C_range=(0.2, 0.2), iters=300, batch=8, lr=3e-3, lam=0.01, C=16, n_layers=4, vth=0.2,
-          seed=0, beta=0.9, log=print):
+          seed=0, beta=0.9, form="spatial", log=print):
     sc_dict = inputs.city_block(seed=21) if scene_kind == "city" else inputs.random_scene(seed=11)
     scene = api.Scene(sc_dict)
     t0 = time.time()
@@ -102,7 +107,7 @@ def train(scene_kind="city", n_clips=32, n_frames=65, size=128, spp_in=2, spp_re
     torch.cuda.synchronize()
     log("data: %d clips x %d frames x %dx%d in %.1f s, %.3f target events per pixel-step"
         % (n_clips, n_frames, size, size, time.time() - t0, float(E.abs().mean())))
-    T = training.Trainer(identity_init(C, n_layers, vth, seed=seed, beta=beta), lr=lr, lam=lam)
+    T = training.Trainer(identity_init(C, n_layers, vth, seed=seed, beta=beta, form=form), lr=lr, lam=lam)
     rng = np.random.default_rng(seed)
     hist = []
     t0 = time.time()
@@ -191,11 +196,14 @@ def main():
     p.add_argument("--c-min", type=float, default=0.2)
     p.add_argument("--c-max", type=float, default=0.2)
     p.add_argument("--beta", type=float, default=0.9, help="BiLIF leak (1 - 1/tau)")
+    p.add_argument("--form", default="spatial", choices=["spatial", "temporal"],
+                   help="3x3 stack of 4 layers, or the paper's temporal form (k = 7, M = 3)")
     p.add_argument("--eval-frames", type=int, default=129)
     p.add_argument("--out", default=os.path.join(HERE, "weights", "evsnet_city.npz"))
     a = p.parse_args()
     T, hist = train(a.scene, a.clips, a.frames, a.size, a.spp_in, a.spp_ref, (a.c_min, a.c_max),
-                    a.iters, lr=a.lr, lam=a.lam, beta=a.beta)
+                    a.iters, lr=a.lr, lam=a.lam, beta=a.beta, form=a.form,
+                    n_layers=7 if a.form == "temporal" else 4)
     net = T.net_dict()
     ev = evaluate(net, a.scene, n_frames=a.eval_frames)
     print("held-out:", ev)

@@ -21,15 +21,19 @@ import torch
 
 pytestmark = pytest.mark.gpu
 
-WEIGHTS = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
-                       "paper_2508_18071_gb300", "weights", "evsnet_city.npz")
+WDIR = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                    "paper_2508_18071_gb300", "weights")
 
 
-def test_trained_evsnet_beats_threshold_on_low_spp():
+@pytest.mark.parametrize("name", ["evsnet_city.npz", "evsnet_city_temporal.npz"])
+def test_trained_evsnet_beats_threshold_on_low_spp(name):
+    """Both trained forms: the 3x3 stack of the workload configurations and the
+    paper's temporal form (kernel 7, 3 residual blocks)."""
     assert torch.cuda.is_available()
     from paper_2508_18071_gb300 import train_evsnet
-    net = train_evsnet.load(WEIGHTS)
-    hist = np.load(WEIGHTS)["train_history"]
+    path = os.path.join(WDIR, name)
+    net = train_evsnet.load(path)
+    hist = np.load(path)["train_history"]
     assert hist[-1, 1] < 0.25 * hist[0, 1]                   # training lowered the loss
     # 129 frames: long enough that a current offset integrating into periodic
     # firing would show up in the event rate
