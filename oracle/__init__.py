@@ -68,6 +68,7 @@ def lib():
                                         P, P, i64]
         L.orc_sensor_events.restype = i64
         L.orc_sensor_thresholds.argtypes = [i64, C.c_double, C.c_double, C.c_uint64, P]
+        L.orc_annotations.argtypes = [P, P, i32, P, i32, i32, P, P, P, P, P]
         L.orc_event_matches.argtypes = [P, i64, P, i64, i32]
         L.orc_event_matches.restype = i64
         L.orc_bsdf_eval.argtypes = [P, P, P, i64, P, P]
@@ -182,6 +183,20 @@ class Scene:
         # rays traced (closest + shadow), BVH nodes visited, triangles tested
         self.rays_traced, self.node_visits, self.tri_tests = (int(v) for v in nr)
         return (rgb, rec) if records else rgb
+
+    def annotations(self, cams, W, H, next_cam=None):
+        """Primary-hit annotations through pixel centres: dict of depth [F,H,W],
+        normal [F,H,W,3], prim [F,H,W] (-1 miss), material [F,H,W] (-1 miss),
+        flow [F,H,W,2] (pixels to the next frame's image)."""
+        cams = _c(cams, np.float32).reshape(-1, 13)
+        F = cams.shape[0]
+        nxt = None if next_cam is None else _c(next_cam, np.float32).reshape(13)
+        out = {"depth": np.empty((F, H, W)), "normal": np.empty((F, H, W, 3)),
+               "prim": np.empty((F, H, W), np.int32), "material": np.empty((F, H, W), np.int64),
+               "flow": np.empty((F, H, W, 2))}
+        lib().orc_annotations(self._h, _p(cams), F, _p(nxt), W, H, _p(out["depth"]), _p(out["normal"]),
+                              _p(out["prim"]), _p(out["material"]), _p(out["flow"]))
+        return out
 
 
 def bsdf_eval(material, wo, wi):

@@ -91,6 +91,13 @@ int64_t orc_sensor_events(const float* logl, int F, int H, int W, double C, doub
                           int64_t* events, int64_t cap);
 void orc_sensor_thresholds(int64_t npix, double C, double sigma, uint64_t seed, double* out);
 
+/* primary-hit annotations through pixel centres (trace.c): depth [F][H][W],
+   normal [F][H][W][3], prim [F][H][W], material [F][H][W] (-1: miss),
+   flow [F][H][W][2]; next_cam: camera after the last frame or NULL */
+void orc_annotations(const orc_scene* s, const float* cams, int F, const float* next_cam, int W,
+                     int H, double* depth, double* normal, int32_t* prim, int64_t* material,
+                     double* flow);
+
 /* number of matched pairs between two event lists [n][4] {x,y,t,p} */
 int64_t orc_event_matches(const int32_t* A, int64_t na, const int32_t* B, int64_t nb, int delta);
 

@@ -591,3 +591,72 @@ void orc_bvh_export(const orc_scene* s, double* bounds, int32_t* links, int32_t*
   }
   for (int64_t i = 0; i < s->n; ++i) perm[i] = s->perm[i];
 }
+
+/* ------------------------------------------------------------- annotations
+ * Per pixel and frame, from the ray through the pixel centre (u = 1/2), the
+ * free by-products of the primary hit (the paper's outputs carry extra
+ * annotations such as depth and segmentation, Sec. 1):
+ *   depth     distance of the hit along the viewing axis -c2 (t cos), +inf on a miss
+ *   normal    unit geometric normal e1 x e2, turned to face the ray (0 on a miss)
+ *   prim      triangle index, -1 on a miss; material: the triangle's material
+ *             word (light triangles: LIGHT_BIT | light index), -1 on a miss
+ *   flow      where the hit point lands in the next frame's image minus this
+ *             pixel's centre, in pixels (x right, y down); NaN on a miss,
+ *             without a next camera, or when the point is behind it
+ * The next camera of frame f is cams[f + 1], and next_cam (may be NULL) for
+ * the last frame. */
+static void project(const float* cam, int W, int H, const double* p, double* xy) {
+  double q[3] = {p[0] - cam[0], p[1] - cam[1], p[2] - cam[2]};
+  double a = q[0]*cam[3] + q[1]*cam[6] + q[2]*cam[9];
+  double b = q[0]*cam[4] + q[1]*cam[7] + q[2]*cam[10];
+  double c = q[0]*cam[5] + q[1]*cam[8] + q[2]*cam[11];
+  if (!(c < 0.0)) { xy[0] = xy[1] = NAN; return; }
+  double th = tan(0.5 * (double)cam[12] * M_PI / 180.0);
+  double px = a / -c, py = b / -c;
+  xy[0] = (px / (th * ((double)W / (double)H)) + 1.0) * 0.5 * W;
+  xy[1] = (1.0 - py / th) * 0.5 * H;
+}
+
+void orc_annotations(const orc_scene* s, const float* cams, int F, const float* next_cam, int W,
+                     int H, double* depth, double* normal, int32_t* prim, int64_t* material,
+                     double* flow) {
+  for (int f = 0; f < F; ++f) {
+    const float* cam = cams + 13 * f;
+    const float* nxt = f + 1 < F ? cams + 13 * (f + 1) : next_cam;
+    double th = tan(0.5 * (double)cam[12] * M_PI / 180.0);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int y = 0; y < H; ++y) {
+      for (int x = 0; x < W; ++x) {
+        int64_t o = ((int64_t)f * H + y) * W + x;
+        double px = (2.0 * (x + 0.5) / W - 1.0) * th * ((double)W / (double)H);
+        double py = (1.0 - 2.0 * (y + 0.5) / H) * th;
+        double dc[3] = {px, py, -1.0}, org[3] = {cam[0], cam[1], cam[2]}, d[3];
+        for (int i = 0; i < 3; ++i) d[i] = cam[3+3*i]*dc[0] + cam[3+3*i+1]*dc[1] + cam[3+3*i+2]*dc[2];
+        normalize3(d);
+        double t; int32_t p;
+        closest(s, org, d, INFINITY, &t, &p, NULL, NULL);
+        prim[o] = p;
+        if (p < 0) {
+          depth[o] = INFINITY;
+          normal[3*o] = normal[3*o+1] = normal[3*o+2] = 0.0;
+          material[o] = -1;
+          flow[2*o] = flow[2*o+1] = NAN;
+          continue;
+        }
+        double axis[3] = {-cam[5], -cam[8], -cam[11]};
+        depth[o] = t * dot3(d, axis);
+        const double* v = s->tri + 9 * (int64_t)p;
+        double e1[3], e2[3], n[3];
+        sub3(v + 3, v, e1); sub3(v + 6, v, e2); cross3(e1, e2, n); normalize3(n);
+        if (dot3(n, d) > 0) { n[0] = -n[0]; n[1] = -n[1]; n[2] = -n[2]; }
+        for (int k = 0; k < 3; ++k) normal[3*o+k] = n[k];
+        material[o] = (int64_t)s->mat[p];
+        if (!nxt) { flow[2*o] = flow[2*o+1] = NAN; continue; }
+        double hp[3] = {org[0] + t*d[0], org[1] + t*d[1], org[2] + t*d[2]}, xy[2];
+        project(nxt, W, H, hp, xy);
+        flow[2*o] = xy[0] - (x + 0.5);
+        flow[2*o+1] = xy[1] - (y + 0.5);
+      }
+    }
+  }
+}
