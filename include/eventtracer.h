@@ -129,6 +129,28 @@ int et_render_frames(const et_scene* scene, const et_camera* cams, int32_t n_fra
                      int32_t max_depth, uint64_t seed, float* rgb, float* logl,
                      int32_t log_mode, float log_param, int32_t* records, void* stream);
 
+/* Annotations of the primary hit through each pixel centre (no jitter), the
+ * by-products that come with the rendered events (the paper's outputs extend
+ * to depth and segmentation, Sec. 1), for n_frames cameras:
+ *   depth     device float [F][H][W]: distance of the hit along the viewing axis
+ *             (t times the cosine to it), +inf on a miss
+ *   normal    device float [F][H][W][3]: unit geometric normal facing the ray,
+ *             0 on a miss
+ *   prim      device int32 [F][H][W]: triangle index in input order (the lights'
+ *             two triangles each follow the user triangles), -1 on a miss
+ *   material  device uint32 [F][H][W]: the triangle's material index (light
+ *             triangles: 0x80000000 | light index), 0xFFFFFFFF on a miss
+ *   flow      device float [F][H][W][2]: position of the hit point in the next
+ *             frame's image minus this pixel's centre, in pixels (x right, y
+ *             down); NaN on a miss, behind the next camera, or for the last
+ *             frame when next_cam (host, may be NULL) is not given
+ * Any output may be NULL (not all).  cams / next_cam: host.  Asynchronous.
+ * Errors: ET_ERR_ARG, ET_ERR_CUDA. */
+int et_render_annotations(const et_scene* scene, const et_camera* cams, int32_t n_frames,
+                          const et_camera* next_cam, int32_t W, int32_t H, float* depth,
+                          float* normal, int32_t* prim, int32_t* material, float* flow,
+                          void* stream);
+
 /* Schedule used by et_render_frames on this scene; both compute identical
  * outputs.  ET_RENDER_WAVEFRONT (default): paths advance one segment at a time
  * through compacted ray queues traced by persistent warps that refill idle

@@ -116,6 +116,36 @@ def render_frames(scene: Scene, cams, W, H, spp, max_depth, seed, first_frame=0,
     return (rgb if want_rgb else None), (logl if want_logl else None), rec
 
 
+def render_annotations(scene: Scene, cams, W: int, H: int, next_cam=None, stream=None,
+                       want=("depth", "normal", "prim", "material", "flow")) -> dict:
+    """et_render_annotations: device tensors depth [F,H,W], normal [F,H,W,3], prim
+    [F,H,W] (int32, -1 miss), material [F,H,W] (int32 holding the uint32 word:
+    lights 0x80000000 | index, 0xFFFFFFFF miss) and flow [F,H,W,2] (pixels to
+    the next camera's image)."""
+    cams = np.ascontiguousarray(cams, np.float32).reshape(-1, 13)
+    F = cams.shape[0]
+    dev = torch.device("cuda")
+    out = {}
+    if "depth" in want:
+        out["depth"] = torch.empty((F, H, W), dtype=torch.float32, device=dev)
+    if "normal" in want:
+        out["normal"] = torch.empty((F, H, W, 3), dtype=torch.float32, device=dev)
+    if "prim" in want:
+        out["prim"] = torch.empty((F, H, W), dtype=torch.int32, device=dev)
+    if "material" in want:
+        out["material"] = torch.empty((F, H, W), dtype=torch.int32, device=dev)
+    if "flow" in want:
+        out["flow"] = torch.empty((F, H, W, 2), dtype=torch.float32, device=dev)
+    nxt = None if next_cam is None else np.ascontiguousarray(next_cam, np.float32).reshape(13)
+    st = L.load().et_render_annotations(scene._h, cams.ctypes.data_as(C.c_void_p), F,
+                                        None if nxt is None else nxt.ctypes.data_as(C.c_void_p), W, H,
+                                        _ptr(out.get("depth")), _ptr(out.get("normal")),
+                                        _ptr(out.get("prim")), _ptr(out.get("material")),
+                                        _ptr(out.get("flow")), _stream(stream))
+    L.check("et_render_annotations", st)
+    return out
+
+
 # ------------------------------------------------------------------ events
 def decode_events(raw: torch.Tensor, n: int) -> np.ndarray:
     """Device et_event buffer (int32 [cap,3]) -> host int32 [n,4] (x, y, t, p)."""
