@@ -23,7 +23,8 @@
  *    produced, only `cap` are stored and *n_events is the full count: the caller
  *    compares after synchronising and retries with a larger buffer.
  *  - Events are emitted in no particular order.
- *  - No call allocates device memory except et_build_scene and the training
+ *  - No call allocates device memory except et_build_scene, the first
+ *    et_scene_update of a scene, and the training
  *    workspace query / et_train_* calls that say so.
  */
 #ifndef EVENTTRACER_H
@@ -102,6 +103,17 @@ int et_build_scene_with(const float* tris, const uint32_t* tri_mat, int64_t n_tr
                         const et_quad_light* lights, int32_t n_lights, float env,
                         int32_t builder, et_scene** out, void* stream);
 void et_scene_free(et_scene* scene);
+/* Moving geometry: new positions for the scene's triangles (host float
+ * [n_tris][9], input order, the same count as at build; the lights stay).  The
+ * hierarchy keeps its topology and its boxes are recomputed bottom-up (refit),
+ * exactly enclosing the new triangles, so closest hits stay exact; its quality
+ * degrades as the motion grows relative to the scene (rebuild then).
+ * et_scene_info's SAH cost is that of the build.  Stream-ordered: renders
+ * queued on `stream` before the call see the old geometry, later ones the new;
+ * do not render the scene on another stream meanwhile.  The first call
+ * allocates a staging buffer of n_tris x 36 bytes owned by the scene.
+ * Errors: ET_ERR_ARG, ET_ERR_OOM, ET_ERR_CUDA. */
+int et_scene_update(et_scene* scene, const float* tris, void* stream);
 /* Which builder produced the hierarchy (ET_BVH_*). */
 int et_scene_builder(const et_scene* scene);
 /* Triangle count (including the lights' triangles), BVH node count and its SAH

@@ -80,6 +80,7 @@ SIGNATURES = {
     "et_kernel_launches": (u64, []),
     "et_sensor_events": (i32, [P, i32, i32, i32, P, i32, P, i32, P, i64, P, P]),
     "et_render_annotations": (i32, [P, P, i32, P, i32, i32, P, P, P, P, P, P]),
+    "et_scene_update": (i32, [P, P, P]),
     "et_set_wait_budget": (None, [i64]),
 }
 

@@ -65,6 +65,16 @@ class Scene:
                                          self.BUILDERS[builder], C.byref(h), _stream(stream))
         L.check("et_build_scene", st)
         self._h = h
+        self.n_user = tris.shape[0]
+
+    def update(self, tris, stream=None):
+        """et_scene_update: new positions (float [n_tris, 9], input order) for the
+        scene's triangles; the hierarchy is refitted."""
+        t = np.ascontiguousarray(tris, np.float32).reshape(-1, 9)
+        if t.shape[0] != self.n_user:
+            raise ValueError("expected %d triangles" % self.n_user)
+        L.check("et_scene_update", L.load().et_scene_update(self._h, t.ctypes.data_as(C.c_void_p),
+                                                             _stream(stream)))
 
     def set_mode(self, mode: int):
         """ET_RENDER_WAVEFRONT (default) or ET_RENDER_MEGAKERNEL."""

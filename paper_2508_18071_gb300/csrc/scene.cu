@@ -282,6 +282,8 @@ extern "C" int et_build_scene_with(const float* tris, const uint32_t* tri_mat, i
   }
   std::vector<BvhNode> hn;
   std::vector<float4> ht((size_t)std::max<int64_t>(n, 1) * 3);
+  std::vector<int32_t> slot_tri((size_t)std::max<int64_t>(n, 1), 0);   // leaf slot -> input triangle
+  std::vector<int> refit_order, refit_levels{0};                        // inner nodes, deepest level first
   int root_ref = -1;   // an empty leaf: first 0, count 0
   double sah = 0.0;
   int64_t n_nodes = 0;
@@ -335,8 +337,27 @@ extern "C" int et_build_scene_with(const float* tris, const uint32_t* tri_mat, i
     }
     n_nodes = (int64_t)bn.size();
     root_ref = ref_of(bn, inner_index, 0);
+    {
+      // refit schedule: inner nodes by depth, deepest first
+      std::vector<std::vector<int>> by_depth;
+      std::vector<std::pair<int, int>> stack{{0, 0}};
+      while (!stack.empty()) {
+        const auto [i, dep] = stack.back();
+        stack.pop_back();
+        if (bn[i].count > 0) continue;
+        if ((int)by_depth.size() <= dep) by_depth.resize(dep + 1);
+        by_depth[dep].push_back(inner_index[i]);
+        stack.push_back({bn[i].left, dep + 1});
+        stack.push_back({bn[i].right, dep + 1});
+      }
+      for (int dep = (int)by_depth.size() - 1; dep >= 0; --dep) {
+        refit_order.insert(refit_order.end(), by_depth[dep].begin(), by_depth[dep].end());
+        refit_levels.push_back((int)refit_order.size());
+      }
+    }
     for (int64_t s = 0; s < n; ++s) {
       int t = perm[s];
+      slot_tri[s] = t;
       const float* p = &v[(size_t)t * 9];
       uint32_t prim = (uint32_t)t, mat = m[t];
       float pf, mf;
@@ -359,6 +380,8 @@ extern "C" int et_build_scene_with(const float* tris, const uint32_t* tri_mat, i
 
   et_scene* s = new et_scene();
   s->n_tris = n; s->n_nodes = n_nodes; s->sah = sah; s->builder = builder;
+  s->n_user = n_tris;
+  s->refit_levels = refit_levels;
   auto fail = [&](int code) { et_scene_free(s); return code; };
   cudaError_t e;
 #define ET_SCENE_ALLOC(ptr, bytes)                                   \
@@ -370,6 +393,8 @@ extern "C" int et_build_scene_with(const float* tris, const uint32_t* tri_mat, i
   ET_SCENE_ALLOC(s->d_lights, sizeof(DevLight) * dl.size());
   s->cam_cap = 1024;
   ET_SCENE_ALLOC(s->d_cams, sizeof(et_camera) * s->cam_cap);
+  ET_SCENE_ALLOC(s->d_perm, sizeof(int32_t) * slot_tri.size());
+  ET_SCENE_ALLOC(s->d_refit, sizeof(int32_t) * std::max<size_t>(refit_order.size(), 1));
 #undef ET_SCENE_ALLOC
 #define ET_SCENE_COPY(dst, src, bytes)                                           \
   e = cudaMemcpyAsync((dst), (src), (bytes), cudaMemcpyHostToDevice, stream);    \
@@ -378,6 +403,9 @@ extern "C" int et_build_scene_with(const float* tris, const uint32_t* tri_mat, i
   ET_SCENE_COPY(s->d_nodes, hn.data(), sizeof(BvhNode) * hn.size());
   ET_SCENE_COPY(s->d_mats, dm.data(), sizeof(DevMaterial) * dm.size());
   ET_SCENE_COPY(s->d_lights, dl.data(), sizeof(DevLight) * dl.size());
+  ET_SCENE_COPY(s->d_perm, slot_tri.data(), sizeof(int32_t) * slot_tri.size());
+  if (!refit_order.empty())
+    ET_SCENE_COPY(s->d_refit, refit_order.data(), sizeof(int32_t) * refit_order.size());
 #undef ET_SCENE_COPY
   e = cudaStreamSynchronize(stream);
   if (e != cudaSuccess) { et_set_last_cuda_error(e); return fail(ET_ERR_CUDA); }
@@ -398,6 +426,9 @@ extern "C" void et_scene_free(et_scene* s) {
   cudaFree(s->d_tris); cudaFree(s->d_nodes); cudaFree(s->d_mats); cudaFree(s->d_lights);
   cudaFree(s->d_cams);
   cudaFree(s->wf_mem);
+  cudaFree(s->d_perm);
+  cudaFree(s->d_refit);
+  cudaFree(s->d_upd);
   delete s;
 }
 

@@ -1,5 +1,6 @@
 // Host-side definition of the opaque et_scene handle.
 #pragma once
+#include <vector>
 #include "et_internal.cuh"
 
 struct et_scene {
@@ -16,4 +17,11 @@ struct et_scene {
   int builder = ET_BVH_GPU;
   void* wf_mem = nullptr;        // wavefront queues and path state, grown on demand
   int64_t wf_cap = 0, wf_acc_cap = 0;
+  // moving geometry (et_scene_update): leaf slot -> input triangle, inner nodes
+  // deepest level first with the level boundaries, upload staging
+  int64_t n_user = 0;
+  int32_t* d_perm = nullptr;
+  int32_t* d_refit = nullptr;
+  std::vector<int> refit_levels;
+  float* d_upd = nullptr;
 };
