@@ -38,7 +38,7 @@
 namespace {
 
 constexpr int TW = 32, TH = 16;
-constexpr int kThreads = 128;
+constexpr int kThreads = 256;         // 8 warps: warp w reads TMEM lanes 32 (w % 4) of the even (w < 4) or odd M blocks
 constexpr uint32_t kWaitIters = 1u << 22;
 int64_t g_wait_budget = -1;          // < 0: kWaitIters
 constexpr unsigned long long kTimeoutBit = 1ull << 62;
@@ -115,7 +115,9 @@ evsnet_tc_kernel(TcParams P, const float* __restrict__ logl, const float* __rest
   const int ox = (blockIdx.x % tiles_x) * TW, oy = (blockIdx.x / tiles_x) * TH;
   const int L = P.L, Wp = P.Wp, Hp = P.Hp, C = P.C;
   const int64_t npix = (int64_t)P.H * P.W;
-  unsigned char* act[2] = {sm, sm + P.off_act1};
+  // one operand buffer, rewritten in place: a layer's epilogue runs after all
+  // of its MMAs have completed
+  unsigned char* act[2] = {sm, sm};
   unsigned char* wB = sm + P.off_wB;
   float* f32 = reinterpret_cast<float*>(sm + P.off_f32);
   float* w0 = f32;                        // [CP][9]
@@ -128,7 +130,7 @@ evsnet_tc_kernel(TcParams P, const float* __restrict__ logl, const float* __rest
   float* Vs = reinterpret_cast<float*>(sm + P.off_V);
 
   // ---- one-time set-up: zero operands, stage weights, membrane potentials
-  for (int i = tid; i < (2 * P.act_bytes) / 16; i += kThreads)
+  for (int i = tid; i < P.act_bytes / 16; i += kThreads)
     reinterpret_cast<uint4*>(sm)[i] = make_uint4(0, 0, 0, 0);
   // packed FP32 weights: layer 0 [C][1][1][3][3], layers 1.. [C][C][1][3][3], projection [C]
   for (int i = tid; i < CP * 9; i += kThreads) {
@@ -298,12 +300,12 @@ evsnet_tc_kernel(TcParams P, const float* __restrict__ logl, const float* __rest
       for (int pass = (kF8 && !last) ? 0 : 1; pass < 2; ++pass) {
         const float inv_next = (kF8 && !last && pass == 1) ? 1.0f / in_scale : 1.0f;
         float amax = 0.0f;
-        for (int b = 0; b < nb; ++b) {
-          const int m = m_start + b * 128 + warp * 32 + lane;
+        for (int b = warp >> 2; b < nb; b += 2) {
+          const int m = m_start + b * 128 + (warp & 3) * 32 + lane;
           float acc[CP];
 #pragma unroll
           for (int jj = 0; jj < CP / 16; ++jj)
-            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + b * CP + jj * 16, acc + jj * 16);
+            tmem_ld16(tmem + ((uint32_t)((warp & 3) * 32) << 16) + b * CP + jj * 16, acc + jj * 16);
           const int py = m / Wp, px = m % Wp;
           const bool need = m < Hp * Wp && py >= l + 1 && py < Hp - l - 1 && px >= l + 1 && px < Wp - l - 1;
           const int gx = ox - L + px, gy = oy - L + py;
@@ -389,8 +391,8 @@ int launch(const float* logl, int32_t F, const et_evsnet_weights* net, et_evsnet
   P.layer_wB = ksteps<CP, kF8>() * 2 * CP * 16;
   P.wB_bytes = (P.L - 1) * P.layer_wB;
   auto al = [](int x) { return (x + 1023) & ~1023; };
-  P.off_act1 = al(P.act_bytes);
-  P.off_wB = P.off_act1 + al(P.act_bytes);
+  P.off_act1 = 0;
+  P.off_wB = al(P.act_bytes);
   P.off_f32 = P.off_wB + al(P.wB_bytes);
   const int f32_bytes = 4 * (CP * 9 + P.L * CP + CP + 4 + P.L * CP);
   P.off_cur = P.off_f32 + al(f32_bytes);
