@@ -73,16 +73,17 @@ __device__ __forceinline__ uint8_t to_e4m3(float v) {
 template <int CP, bool kF8>
 __device__ __forceinline__ void store_row(unsigned char* buf, int plane, int m, const float* v) {
   if constexpr (kF8) {
-    __align__(16) uint8_t h[CP];
+    __align__(16) __nv_fp8x2_storage_t h[CP / 2];
 #pragma unroll
-    for (int c = 0; c < CP; ++c) h[c] = to_e4m3(v[c]);
+    for (int c = 0; c < CP / 2; ++c)
+      h[c] = __nv_cvt_float2_to_fp8x2(make_float2(v[2 * c], v[2 * c + 1]), __NV_SATFINITE, __NV_E4M3);
 #pragma unroll
     for (int p = 0; p < CP / 16; ++p)
       *reinterpret_cast<uint4*>(buf + p * plane + m * 16) = reinterpret_cast<const uint4*>(h)[p];
   } else {
-    __align__(16) __nv_bfloat16 h[CP];
+    __align__(16) __nv_bfloat162 h[CP / 2];
 #pragma unroll
-    for (int c = 0; c < CP; ++c) h[c] = __float2bfloat16_rn(v[c]);
+    for (int c = 0; c < CP / 2; ++c) h[c] = __floats2bfloat162_rn(v[2 * c], v[2 * c + 1]);
 #pragma unroll
     for (int p = 0; p < CP / 8; ++p)
       *reinterpret_cast<uint4*>(buf + p * plane + m * 16) = reinterpret_cast<const uint4*>(h)[p];
@@ -125,6 +126,7 @@ evsnet_tc_kernel(TcParams P, const float* __restrict__ logl, const float* __rest
   float* wp = bs + L * CP;                // [CP] projection
   float* bp = wp + CP;                    // [1] (+ padding)
   float* sw = bp + 4;                     // [L][CP] FP8 weight scales
+  float* l0b = sw + L * CP;               // [CP] sum_t |w0[c][t]| (FP8 layer-0 bound)
   float* cur = reinterpret_cast<float*>(sm + P.off_cur);
   float* prev = reinterpret_cast<float*>(sm + P.off_prev);
   float* Vs = reinterpret_cast<float*>(sm + P.off_V);
@@ -136,6 +138,12 @@ evsnet_tc_kernel(TcParams P, const float* __restrict__ logl, const float* __rest
   for (int i = tid; i < CP * 9; i += kThreads) {
     const int c = i / 9, t = i % 9;
     w0[i] = c < C ? wg[c * 9 + t] : 0.0f;
+  }
+  for (int c = tid; c < CP; c += kThreads) {
+    float a = 0.0f;
+    if (c < C)
+      for (int t = 0; t < 9; ++t) a += fabsf(wg[c * 9 + t]);
+    l0b[c] = a;
   }
   for (int i = tid; i < L * CP; i += kThreads) {
     const int l = i / CP, c = i % CP;
@@ -183,7 +191,7 @@ evsnet_tc_kernel(TcParams P, const float* __restrict__ logl, const float* __rest
     prev[i] = v;
   }
   if (warp == 0) tmem_alloc(&tmem_slot, P.tmem_cols);
-  if (tid == 0) { mbar_init(&mma_bar, 1); bail = 0; }
+  if (tid == 0) { mbar_init(&mma_bar, 1); bail = 0; amax_bits = 0u; }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -192,17 +200,30 @@ evsnet_tc_kernel(TcParams P, const float* __restrict__ logl, const float* __rest
   const uint32_t idesc = kF8 ? umma_idesc_e4m3(128, CP) : umma_idesc_bf16(128, CP);
 
   for (int f = (P.f0 == 0 ? 0 : 1); f < P.F && !bail; ++f) {
-    // ---- frame tile and layer 0 on CUDA cores (FP8: a first pass finds the scale)
+    // ---- frame tile and layer 0 on CUDA cores.  FP8: layer 0's input scale
+    // comes from a bound, |h_c| <= |b_c| + max|X| sum_t |w0[c][t]|, over the
+    // tile's log differences (E4M3's range absorbs the slack)
+    float amx = 0.0f;
     for (int i = tid; i < Hp * Wp; i += kThreads) {
       const int gx = ox - L + i % Wp, gy = oy - L + i / Wp;
-      cur[i] = (gx >= 0 && gx < P.W && gy >= 0 && gy < P.H)
-                   ? __ldg(logl + (int64_t)f * npix + (int64_t)gy * P.W + gx) : 0.0f;
+      const float v = (gx >= 0 && gx < P.W && gy >= 0 && gy < P.H)
+                          ? __ldg(logl + (int64_t)f * npix + (int64_t)gy * P.W + gx) : 0.0f;
+      cur[i] = v;
+      if (kF8) amx = fmaxf(amx, fabsf(v - prev[i]));
     }
-    if (tid == 0) amax_bits = 0u;
+    if (kF8) atomicMax(&amax_bits, __float_as_uint(amx));
     __syncthreads();
-    for (int pass = kF8 ? 0 : 1; pass < 2; ++pass) {
+    if (kF8) {
+      if (tid == 0) {
+        const float xm = __uint_as_float(amax_bits);
+        float bound = 0.0f;
+        for (int c = 0; c < C; ++c) bound = fmaxf(bound, fabsf(bs[c]) + xm * l0b[c]);
+        in_scale = e4m3_scale(bound);
+      }
+      __syncthreads();
+    }
+    {
       const float inv = kF8 ? 1.0f / in_scale : 1.0f;
-      float amax = 0.0f;
       for (int i = tid; i < (Hp - 2) * (Wp - 2); i += kThreads) {
         const int py = 1 + i / (Wp - 2), px = 1 + i % (Wp - 2);
         const int gx = ox - L + px, gy = oy - L + py;
@@ -222,25 +243,16 @@ evsnet_tc_kernel(TcParams P, const float* __restrict__ logl, const float* __rest
 #pragma unroll
             for (int t = 0; t < 9; ++t) a = fmaf(w0[c * 9 + t], x[t], a);
             h[c] = fmaxf(a, 0.0f);
-            amax = fmaxf(amax, h[c]);
           }
         } else {
 #pragma unroll
           for (int c = 0; c < CP; ++c) h[c] = 0.0f;
         }
-        if (pass == 1) {
-          if (kF8) {
+        if (kF8) {
 #pragma unroll
-            for (int c = 0; c < CP; ++c) h[c] *= inv;
-          }
-          store_row<CP, kF8>(act[0], P.plane, m, h);
+          for (int c = 0; c < CP; ++c) h[c] *= inv;
         }
-      }
-      if (pass == 0) {
-        atomicMax(&amax_bits, __float_as_uint(amax));
-        __syncthreads();
-        if (tid == 0) in_scale = e4m3_scale(__uint_as_float(amax_bits));
-        __syncthreads();
+        store_row<CP, kF8>(act[0], P.plane, m, h);
       }
     }
     if (!kF8 && tid == 0) in_scale = 1.0f;
@@ -355,6 +367,7 @@ evsnet_tc_kernel(TcParams P, const float* __restrict__ logl, const float* __rest
       }
       tc_fence_before();
     }
+    if (tid == 0) amax_bits = 0u;
     __syncthreads();
     float* t = cur; cur = prev; prev = t;
   }
@@ -394,7 +407,7 @@ int launch(const float* logl, int32_t F, const et_evsnet_weights* net, et_evsnet
   P.off_act1 = 0;
   P.off_wB = al(P.act_bytes);
   P.off_f32 = P.off_wB + al(P.wB_bytes);
-  const int f32_bytes = 4 * (CP * 9 + P.L * CP + CP + 4 + P.L * CP);
+  const int f32_bytes = 4 * (CP * 9 + P.L * CP + CP + 4 + P.L * CP + CP);
   P.off_cur = P.off_f32 + al(f32_bytes);
   P.off_prev = P.off_cur + al(4 * P.Hp * P.Wp);
   P.off_V = P.off_prev + al(4 * P.Hp * P.Wp);
