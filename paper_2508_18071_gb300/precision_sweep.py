@@ -1,0 +1,99 @@
+"""The EvSNet precision sweep: the same rendered frames (1280 x 720 city block,
+1 SPP, 2000 frames by default) through the EvSNet convolutions in FP32, BF16
+and FP8 (E4M3 with power-of-two scales, FP32 accumulation), reporting per
+precision the device time, throughput, event count, event F1 against the FP32
+output (matching per pixel and step, delta = 0) and the bidirectional EMD to
+the FP32 output (the paper's Eq. 8-9, averaged over pixels).
+
+    python -m paper_2508_18071_gb300.precision_sweep [--frames 2000] [--spp 1]
+
+Prints one JSON object.  Networks: the trained city network and a random-init
+one of the same shape (N(0, 0.1) weights, Vth 0.5, leak 0.9).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import time
+
+import torch
+
+from . import _lib as L
+from . import api, inputs, training
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def _time(fn, reps=3):
+    ts = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return min(ts)
+
+
+def sweep(logl: torch.Tensor, net_d: dict, cap=1 << 20) -> dict:
+    F, H, W = logl.shape
+    K = F - 1
+    C, Ln = net_d["C"], net_d["n_layers"]
+    flops = 2.0 * (9 * C + (Ln - 1) * 9 * C * C + C) * H * W * K
+    out, ref = {}, None
+    buf = api.EventBuffer(cap)
+    for name, dt in (("f32", L.ET_F32), ("bf16", L.ET_BF16), ("fp8", L.ET_FP8)):
+        net = api.EvsNetDev.from_dict(net_d, dt)
+        holder = {}
+
+        def call():
+            holder["S"] = api.evsnet_forward(logl, net, api.EvsStateDev(net, H, W), buf=buf,
+                                             want_spikes=True)[2]
+        # timed with the dense spike output (1 B per pixel-step) the metrics need
+        ms = _time(call, reps=1 if dt == L.ET_F32 else 3)
+        S = holder.pop("S")
+        n = int((S != 0).sum().item())
+        if ref is None:
+            ref = S
+        match = int(((S == ref) & (S != 0)).sum().item())
+        n_ref = int((ref != 0).sum().item())
+        f1 = 1.0 if n + n_ref == 0 else 2.0 * match / (n + n_ref)
+        loss, _, _ = training.emd_count_loss(S.unsqueeze(0), ref.unsqueeze(0).float(), 0.0)
+        out[name] = {"ms_per_frame": ms / K, "tflops": flops / (ms / 1e3) / 1e12, "events": n,
+                     "f1_vs_f32": f1, "emd_vs_f32": float(loss[1].item())}
+        del S
+    return out
+
+
+def main():
+    p = argparse.ArgumentParser()
+    p.add_argument("--frames", type=int, default=2000)
+    p.add_argument("--spp", type=int, default=1)
+    p.add_argument("--width", type=int, default=1280)
+    p.add_argument("--height", type=int, default=720)
+    p.add_argument("--chunk", type=int, default=200)
+    a = p.parse_args()
+    from . import train_evsnet
+    scene = api.Scene(inputs.city_block(seed=21))
+    path = inputs.city_path(a.frames)
+    logl = torch.empty((a.frames, a.height, a.width), dtype=torch.float32, device="cuda")
+    t0 = time.time()
+    for f0 in range(0, a.frames, a.chunk):
+        f1 = min(a.frames, f0 + a.chunk)
+        api.render_frames(scene, path[f0:f1], a.width, a.height, a.spp, 5, 0, first_frame=f0,
+                          logl=logl[f0:f1], want_rgb=False)
+    torch.cuda.synchronize()
+    res = {"workload": "city block 500k triangles, %dx%d, %d frames at 1 kHz, %d SPP, depth 5"
+                       % (a.width, a.height, a.frames, a.spp),
+           "render_s": time.time() - t0}
+    trained = train_evsnet.load(os.path.join(HERE, "weights", "evsnet_city.npz"))
+    rand = inputs.random_evsnet(0, 4, 16, 1, 3, seed=12, vth=0.5, beta=0.9)
+    res["trained"] = sweep(logl, trained)
+    res["random_init"] = sweep(logl, rand)
+    print(json.dumps(res))
+
+
+if __name__ == "__main__":
+    main()
