@@ -417,13 +417,26 @@ def main():
         line["cpu_baseline"] = cpu
         flops_launch = work["flops_per_ray"] * work["rays_per_sample"] * npix * args.spp * F
         line["mrays_per_s"] = work["rays_per_sample"] * npix * args.spp * F / (statistics.mean(t_render) / 1e3) / 1e6
+        # the survey's second traversal bound: algorithmic node + triangle bytes
+        # per ray against HBM (above 1: the hierarchy is served from L1 / L2)
+        bytes_launch = work["bytes_per_ray"] * work["rays_per_sample"] * npix * args.spp * F
+        hbm = peaks.get("hbm_gbs") or 6800.0
+        line["roofline_traversal_bytes"] = {
+            "bound": "hbm", "achieved": bytes_launch / (statistics.mean(t_render) / 1e3) / 1e9,
+            "peak": hbm, "unit": "GB/s",
+            "frac": bytes_launch / (statistics.mean(t_render) / 1e3) / 1e9 / hbm,
+            "work": "64 B per node visit + 36 B per triangle test (%.0f B/ray)" % work["bytes_per_ray"],
+            "peak_source": "MEASURED_PEAKS hbm_gbs (of measured)" if "hbm_gbs" in peaks
+                           else "fallback 6.8 TB/s",
+            "note": "algorithmic bytes; the measured DRAM traffic of wf_trace is ~1 % of its "
+                    "peak (profiles/wf_trace_v3_city320x180.md): L1 / L2 serve them"}
         t_launch = statistics.mean(t_render) / 1e3
         peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * 2.07e9 / 1e12
         line["roofline"] = {"bound": "alu", "achieved": flops_launch / t_launch / 1e12,
                             "peak": peak, "unit": "TFLOP/s",
                             "frac": flops_launch / t_launch / 1e12 / peak, "traffic": None,
                             "kernel": "wavefront render (wf_trace closest/shadow, wf_shade, "
-                                      "wf_raygen, wf_accumulate); wf_trace ~88 % of it",
+                                      "wf_raygen, wf_accumulate); wf_trace ~81 % of it",
                             "work": "24 flop per BVH node visit + 40 per triangle test, counted by "
                                     "the oracle's full-sweep SAH BVH on the sampled rays (%.1f "
                                     "rays/sample, %.0f flop/ray)" % (work["rays_per_sample"],
