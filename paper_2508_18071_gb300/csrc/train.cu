@@ -625,9 +625,16 @@ extern "C" int et_evsnet_train_backward_static(const float* logl, const et_train
                                                float* grad_w, float* grad_b, void* stream) {
   int rc = check(net, sh);
   if (rc != ET_OK) return rc;
-  Workspace ws{};
-  layout(net, sh, nullptr, &ws);
-  if (ws.bytes > kStaticWorkspaceBytes) return ET_ERR_CAPACITY;   // shape too large for the array
+  // scratch of either form (the temporal one keeps whole-clip activations)
+  size_t need = 0;
+  if (et_train_is_temporal(net)) {
+    need = et_train_temporal_bytes(net, sh);
+  } else {
+    Workspace ws{};
+    layout(net, sh, nullptr, &ws);
+    need = ws.bytes;
+  }
+  if (need > kStaticWorkspaceBytes) return ET_ERR_CAPACITY;   // shape too large for the array
   int dev = 0;
   ET_CHECK_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDevices) return ET_ERR_ARG;
@@ -643,7 +650,8 @@ extern "C" int et_evsnet_train_backward_static(const float* logl, const et_train
     base = g_static_ws[dev];
   }
   // the backward clears the part of the scratch that must start at zero (the
-  // carried membrane gradient) and overwrites the rest before reading it
+  // carried membrane gradient of the spatial form) and overwrites the rest
+  // before reading it
   return et_evsnet_train_backward(logl, sh, net, V_ckpt, dS_on, dS_off, alpha, grad_w, grad_b, base,
                                   kStaticWorkspaceBytes, stream);
 }

@@ -64,3 +64,42 @@ def test_static_workspace_backward_matches_workspace_backward():
         C.c_void_p(lfd.data_ptr()), C.byref(big), C.byref(net), C.c_void_p(out["V_ckpt"].data_ptr()),
         C.c_void_p(dSon.data_ptr()), C.c_void_p(dSoff.data_ptr()), 2.0, C.c_void_p(gw.data_ptr()),
         C.c_void_p(gb.data_ptr()), stream) == _lib.ET_ERR_CAPACITY
+
+
+def test_static_workspace_backward_temporal_form():
+    """The same check for the paper's temporal form (kernel 7 along time, one
+    residual block), whose scratch holds whole-clip activations; a clip too long
+    for the array is refused with ET_ERR_CAPACITY."""
+    assert torch.cuda.is_available()
+    from paper_2508_18071_gb300 import _lib, api, training
+    lib = _lib.load()
+    B, K, H, W, ck = 1, 20, 16, 16, 8
+    d = inputs.random_evsnet(1, 3, 8, 7, 1, seed=9, vth=0.3, beta=0.9, std=0.3)
+    lf = np.stack([inputs.random_logl_clip(60 + b, K + 1, H, W, step_std=0.3) for b in range(B)])
+    E = np.random.default_rng(5).choice([-1, 0, 0, 0, 1], (B, K, H, W)).astype(np.float32)
+    meta = api.EvsNetDev.from_dict(d)
+    lfd, Ed = torch.as_tensor(lf).cuda(), torch.as_tensor(E).cuda()
+    out = training.train_forward(lfd, meta, meta.w, meta.b, ckpt_every=ck)
+    _, dSon, dSoff = training.emd_count_loss(out["spikes"], Ed, 0.01)
+    ref_w, ref_b = training.train_backward(lfd, meta, meta.w, meta.b, out["V_ckpt"], dSon, dSoff,
+                                           ckpt_every=ck)
+    ref = torch.cat([ref_w, ref_b]).cpu().numpy()
+    assert np.abs(ref).max() > 0
+    sh = _lib.et_train_shape(B, K, H, W, ck)
+    net = _lib.et_evsnet_weights(meta.kind, meta.n_layers, meta.C, meta.kt, meta.ks, meta.beta,
+                                 meta.vth, meta.reset, _lib.ET_F32, meta.w.data_ptr(), meta.b.data_ptr())
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    args = lambda gw, gb, shape: (C.c_void_p(lfd.data_ptr()), C.byref(shape), C.byref(net),
+                                  C.c_void_p(out["V_ckpt"].data_ptr()), C.c_void_p(dSon.data_ptr()),
+                                  C.c_void_p(dSoff.data_ptr()), 2.0, C.c_void_p(gw.data_ptr()),
+                                  C.c_void_p(gb.data_ptr()), stream)
+    for call in range(2):
+        gw = torch.zeros_like(meta.w)
+        gb = torch.zeros_like(meta.b)
+        st = lib.et_evsnet_train_backward_static(*args(gw, gb, sh))
+        assert st == _lib.ET_OK, lib.et_status_str(st)
+        torch.cuda.synchronize()
+        got = torch.cat([gw, gb]).cpu().numpy()
+        assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max(), (call, np.abs(got - ref).max())
+    big = _lib.et_train_shape(8, 64, 128, 128, 16)
+    assert lib.et_evsnet_train_backward_static(*args(gw, gb, big)) == _lib.ET_ERR_CAPACITY
