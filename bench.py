@@ -53,6 +53,9 @@ def parse():
                    help="hierarchy builder (default: the library's)")
     p.add_argument("--no-sweep", action="store_true",
                    help="skip the EvSNet precision sweep (FP32 / BF16 / FP8) after the timed region")
+    p.add_argument("--rows", action="store_true",
+                   help="measure the rows beside the benchmark's path (event generators, "
+                        "annotations, refit, training, FP32 EvSNet) instead of the metric")
     p.add_argument("--width", type=int, default=1280, help="smaller sizes: profiling cases only")
     p.add_argument("--height", type=int, default=720)
     return p.parse_args()
@@ -235,6 +238,156 @@ def precision_sweep(api, _lib, net_d, logl, stream, reps=5):
     return out
 
 
+def run_rows(args):
+    """--rows: the rows beside the benchmark's path, each timed on the GPU with
+    CUDA events against its bound and next to the oracle on a bounded host sample
+    (extrapolated per unit).  Prints one JSON line."""
+    import numpy as np
+    import torch
+    import oracle
+    from paper_2508_18071_gb300 import api, inputs, training, _lib, train_evsnet
+    dev = torch.device("cuda", 0)
+    props = torch.cuda.get_device_properties(dev)
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm = peaks.get("hbm_gbs") or 6800.0
+    fp32 = props.multi_processor_count * FP32_LANES_PER_SM * 2 * 2.07e9 / 1e12
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    W, H, F = W_, H_, 50
+    npix = W * H
+
+    def gtime(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) / 1e3)
+        return min(ts)
+
+    def ctime(fn):
+        t0 = time.perf_counter()
+        fn()
+        return time.perf_counter() - t0
+
+    scene = inputs.city_block(seed=21)
+    g = api.Scene(scene)
+    path = inputs.city_path(F + 1, first=400)
+    logl = torch.empty((F, H, W), dtype=torch.float32, device=dev)
+    api.render_frames(g, path[:F], W, H, 2, DEPTH, SEED, first_frame=400, logl=logl, want_rgb=False)
+    lf_host = logl[:4].cpu().numpy()
+    rows = {}
+
+    # a10: contrast-threshold events (bytes: log frames in, FP64 state in/out, events out)
+    buf = api.EventBuffer(F * npix)
+    ref = torch.zeros(npix, dtype=torch.float64, device=dev)
+    t = gtime(lambda: api.threshold_events(logl, C_THR, ref.zero_(), False, buf=buf))
+    nev = buf.n()
+    byts = 4.0 * F * npix + 16.0 * npix + 12.0 * nev
+    tc = ctime(lambda: oracle.threshold_events(lf_host, C_THR, oracle.ThresholdState.new(H, W)))
+    rows["threshold_events"] = {
+        "ms_per_frame": t * 1e3 / F, "roofline": {"bound": "hbm", "achieved": byts / t / 1e9,
+                                                  "peak": hbm, "unit": "GB/s", "frac": byts / t / 1e9 / hbm},
+        "cpu_baseline": {"ms_per_frame": tc * 1e3 / 3, "cores": 1, "kind": "oracle",
+                         "sample": "4 frames of 720p"}}
+
+    # sensor model, every non-ideality on
+    sp = api.SensorParams(C=0.2, sigma_C=0.1, refractory_us=300.0, leak_hz=40.0, shot_hz=25.0, seed=3)
+    sst = api.SensorStateDev(H, W)
+
+    def sensor():
+        sst.initialized = 0
+        api.sensor_events(logl, sp, sst, buf=buf)
+    t = gtime(sensor)
+    nev = buf.n()
+    byts = 4.0 * F * npix + 24.0 * npix + 12.0 * nev
+    osp = oracle.SensorParams(C=0.2, sigma_C=0.1, refractory_us=300.0, leak_hz=40.0, shot_hz=25.0, seed=3)
+    tc = ctime(lambda: oracle.sensor_events(lf_host, osp, oracle.SensorState.new(H, W)))
+    rows["sensor_events"] = {
+        "ms_per_frame": t * 1e3 / F, "events_per_pixel_step": nev / (npix * (F - 1)),
+        "roofline": {"bound": "hbm", "achieved": byts / t / 1e9, "peak": hbm, "unit": "GB/s",
+                     "frac": byts / t / 1e9 / hbm,
+                     "note": "bytes bound; every decision is FP64 (each step simulated twice)"},
+        "cpu_baseline": {"ms_per_frame": tc * 1e3 / 3, "cores": 1, "kind": "oracle",
+                         "sample": "4 frames of 720p"}}
+
+    # primary-hit annotations: one ray per pixel and frame
+    t = gtime(lambda: api.render_annotations(g, path[:10], W, H, next_cam=path[10]))
+    o = oracle.Scene(scene["tris"], scene["tri_mat"], scene["materials"], scene["lights"], scene["env"])
+    crop = 32
+    tc = ctime(lambda: o.annotations(path[:1], W, crop, next_cam=path[1]))
+    rows["annotations"] = {"ms_per_frame": t * 1e3 / 10, "mrays_per_s": 10 * npix / t / 1e6,
+                           "cpu_baseline": {"ms_per_frame": tc * 1e3 * H / crop, "cores": cores,
+                                            "kind": "oracle", "sample": "1 frame, %d rows of 1280 px "
+                                            "(same camera model, rays through the top rows)" % crop}}
+
+    # refit after moving geometry (500k triangles from host memory)
+    tris = np.ascontiguousarray(scene["tris"], np.float32)
+    t = gtime(lambda: g.update(tris))
+    tb = ctime(lambda: oracle.Scene(scene["tris"], scene["tri_mat"], scene["materials"],
+                                    scene["lights"], scene["env"]))
+    rows["scene_update_refit"] = {"ms_per_update": t * 1e3, "triangles": len(tris),
+                                  "note": "includes the 18 MB host-to-device copy of the positions",
+                                  "cpu_baseline": {"ms_per_update": tb * 1e3, "cores": 1, "kind": "oracle",
+                                                   "sample": "the oracle rebuilds its full-sweep BVH"}}
+
+    # training steps at the workload's training shape: 8 clips x 64 steps x 128 x 128
+    B, K, S = 8, 64, 128
+    clips = torch.stack([torch.as_tensor(inputs.random_logl_clip(70 + b, K + 1, S, S, step_std=0.1))
+                         for b in range(B)]).cuda()
+    E = torch.as_tensor(np.random.default_rng(1).choice([-1, 0, 0, 0, 0, 0, 1], (B, K, S, S))
+                        .astype(np.float32)).cuda()
+    for name, d in (("training_step_3x3", inputs.random_evsnet(0, 4, 16, 1, 3, seed=2, vth=0.2, beta=0.9)),
+                    ("training_step_temporal", inputs.random_evsnet(1, 7, 16, 7, 1, seed=2, vth=0.2,
+                                                                      beta=0.9, std=0.05))):
+        T = training.Trainer(d, lr=1e-3)
+        t = gtime(lambda: T.step(clips, E))
+        C_, Ln, kt, ks = d["C"], d["n_layers"], d["kt"], d["ks"]
+        macs = kt * ks * ks * C_ + (Ln - 1) * kt * ks * ks * C_ * C_ + C_
+        # forward, its recompute in the backward, data and weight gradients
+        flops = 4 * 2.0 * macs * B * K * S * S
+        onet = oracle.EvsNet(d["kind"], Ln, C_, kt, ks, d["beta"], d["vth"], d["reset"],
+                             np.asarray(d["w"], float), np.asarray(d["b"], float))
+        xs = np.diff(np.asarray(clips[:1, :17, :32, :32].cpu().numpy(), np.float64), axis=1)
+        es = E[:1, :16, :32, :32].cpu().numpy().astype(np.float64)
+        tc = ctime(lambda: oracle.torch_grads(xs, es, onet))
+        rows[name] = {"ms_per_step": t * 1e3, "pixel_steps": B * K * S * S,
+                      "roofline": {"bound": "alu", "achieved": flops / t / 1e12, "peak": fp32,
+                                   "unit": "TFLOP/s", "frac": flops / t / 1e12 / fp32,
+                                   "work": "4 x %d MAC per pixel-step (forward, recomputed forward, "
+                                           "data and weight gradients)" % macs},
+                      "cpu_baseline": {"ms_per_step": tc * 1e3 * (B * K * S * S) / (16 * 32 * 32),
+                                       "kind": "oracle (float64 torch autograd)",
+                                       "cores": torch.get_num_threads(),
+                                       "sample": "1 clip x 16 steps x 32 x 32, extrapolated"}}
+
+    # EvSNet FP32 (the parity path of every form) at 720p
+    trained = train_evsnet.load(os.path.join(ROOT, "paper_2508_18071_gb300", "weights", "evsnet_city.npz"))
+    temporal = train_evsnet.load(os.path.join(ROOT, "paper_2508_18071_gb300", "weights",
+                                              "evsnet_city_temporal.npz"))
+    for name, d in (("evsnet_f32_3x3", trained), ("evsnet_f32_temporal", temporal)):
+        net = api.EvsNetDev.from_dict(d, _lib.ET_F32)
+        t = gtime(lambda: api.evsnet_forward(logl[:11], net, api.EvsStateDev(net, H, W), buf=buf), reps=2)
+        C_, Ln, kt, ks = d["C"], d["n_layers"], d["kt"], d["ks"]
+        macs = kt * ks * ks * C_ + (Ln - 1) * kt * ks * ks * C_ * C_ + C_
+        flops = 2.0 * macs * npix * 10
+        onet = oracle.EvsNet(d["kind"], Ln, C_, kt, ks, d["beta"], d["vth"], d["reset"],
+                             np.asarray(d["w"], float), np.asarray(d["b"], float))
+        tc = ctime(lambda: oracle.evsnet_forward(lf_host[:, :64, :64], onet,
+                                                 oracle.EvsState.new(onet, 64, 64), nthreads=cores))
+        rows[name] = {"ms_per_frame": t * 1e3 / 10,
+                      "roofline": {"bound": "alu", "achieved": flops / t / 1e12, "peak": fp32,
+                                   "unit": "TFLOP/s", "frac": flops / t / 1e12 / fp32},
+                      "cpu_baseline": {"ms_per_frame": tc * 1e3 / 3 * npix / (64 * 64), "cores": cores,
+                                       "kind": "oracle", "sample": "64 x 64 crop, 3 steps"}}
+    print(json.dumps({"mode": "rows", "gpu": props.name, "fp32_peak_tflops": fp32,
+                      "hbm_peak_gbs": hbm, "rows": rows}))
+
+
 def load_net_host():
     from paper_2508_18071_gb300 import inputs, train_evsnet
     path = os.path.join(ROOT, "paper_2508_18071_gb300", "weights", "evsnet_city.npz")
@@ -251,6 +404,9 @@ def main():
     W_, H_ = args.width, args.height
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.rows:
+        run_rows(args)
         return
     import numpy as np
     import torch

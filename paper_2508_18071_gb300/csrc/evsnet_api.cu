@@ -1,5 +1,6 @@
-// et_evsnet_forward: argument checks and dispatch between the FP32 (CUDA core)
-// and BF16 / FP8 (tensor core) EvSNet kernels.
+// et_evsnet_forward: argument checks and dispatch between the FP32 (CUDA core:
+// pixel-wise form in evsnet_pix.cu, spatial forms in evsnet.cu) and BF16 / FP8
+// (tensor core) EvSNet kernels.
 #include "et_internal.cuh"
 #include "evsnet_common.h"
 
@@ -24,7 +25,9 @@ extern "C" int et_evsnet_forward(const float* logl, int32_t F, const et_evsnet_w
   ET_CHECK_CUDA(cudaMemsetAsync(n_events, 0, sizeof(int64_t), stream));
   if (F == 0) return ET_OK;
   int rc;
-  if (net->dtype == ET_F32)
+  if (net->dtype == ET_F32 && net->ks == 1)
+    rc = et_evsnet_forward_pix(logl, F, net, st, t0, events, cap, n_events, I_out, spikes, stream);
+  else if (net->dtype == ET_F32)
     rc = et_evsnet_forward_f32(logl, F, net, st, t0, events, cap, n_events, I_out, spikes, stream);
   else if (net->dtype == ET_BF16 || net->dtype == ET_FP8)
     rc = et_evsnet_forward_tc(logl, F, net, st, t0, events, cap, n_events, I_out, spikes, stream);
