@@ -18,7 +18,7 @@
 
 namespace {
 
-constexpr int kThreads = 128;
+constexpr int kThreads = 256;
 constexpr int kMaxKt = 9;
 
 struct PixParams {
@@ -78,13 +78,31 @@ evsnet_pix_kernel(PixParams P, const float* __restrict__ logl, const float* __re
         const float* wl = sw + l * kt * CP * CP;
 #pragma unroll
         for (int co = 0; co < CP; ++co) acc[co] = sb[l * CP + co];
+        // software pipeline: the next tap's inputs are loaded while this
+        // tap's products accumulate
+        float nxt[CP];
+        {
+          const int slot0 = head < hk ? head : head - hk;
+#pragma unroll
+          for (int ci = 0; ci < CP; ++ci)
+            nxt[ci] = ci >= cin ? 0.0f : (0 == hk ? x[ci] : hist[hidx(l, slot0, ci)]);
+        }
         for (int tau = 0; tau < kt; ++tau) {
           const float* wt = wl + tau * CP * CP;
-          const int slot = head + tau < hk ? head + tau : head + tau - hk;
+          float in[CP];
+#pragma unroll
+          for (int ci = 0; ci < CP; ++ci) in[ci] = nxt[ci];
+          if (tau + 1 < kt) {
+            const int t1 = tau + 1;
+            const int slot1 = head + t1 < hk ? head + t1 : head + t1 - hk;
+#pragma unroll
+            for (int ci = 0; ci < CP; ++ci)
+              nxt[ci] = ci >= cin ? 0.0f : (t1 == hk ? x[ci] : hist[hidx(l, slot1, ci)]);
+          }
 #pragma unroll
           for (int ci = 0; ci < CP; ++ci) {
             if (ci >= cin) break;
-            const float v = tau == hk ? x[ci] : hist[hidx(l, slot, ci)];
+            const float v = in[ci];
             const float4* w4 = reinterpret_cast<const float4*>(wt + ci * CP);
 #pragma unroll
             for (int j = 0; j < CP / 4; ++j) {
