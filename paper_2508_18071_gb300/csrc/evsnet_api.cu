@@ -1,6 +1,7 @@
 // et_evsnet_forward: argument checks and dispatch between the FP32 (CUDA core:
-// pixel-wise form in evsnet_pix.cu, spatial forms in evsnet.cu) and BF16 / FP8
-// (tensor core) EvSNet kernels.
+// pixel-wise form in evsnet_pix.cu, 3x3 stacks of up to 16 channels in
+// evsnet_f32s.cu, other spatial forms in evsnet.cu) and BF16 / FP8 (tensor
+// core) EvSNet kernels.
 #include "et_internal.cuh"
 #include "evsnet_common.h"
 
@@ -27,8 +28,12 @@ extern "C" int et_evsnet_forward(const float* logl, int32_t F, const et_evsnet_w
   int rc;
   if (net->dtype == ET_F32 && net->ks == 1)
     rc = et_evsnet_forward_pix(logl, F, net, st, t0, events, cap, n_events, I_out, spikes, stream);
-  else if (net->dtype == ET_F32)
-    rc = et_evsnet_forward_f32(logl, F, net, st, t0, events, cap, n_events, I_out, spikes, stream);
+  else if (net->dtype == ET_F32) {
+    // the 3x3 kernel declines (before launching anything) what it does not cover
+    rc = et_evsnet_forward_f32s(logl, F, net, st, t0, events, cap, n_events, I_out, spikes, stream);
+    if (rc == ET_ERR_UNIMPLEMENTED)
+      rc = et_evsnet_forward_f32(logl, F, net, st, t0, events, cap, n_events, I_out, spikes, stream);
+  }
   else if (net->dtype == ET_BF16 || net->dtype == ET_FP8)
     rc = et_evsnet_forward_tc(logl, F, net, st, t0, events, cap, n_events, I_out, spikes, stream);
   else
