@@ -36,17 +36,15 @@ struct Net {
 
 __host__ __device__ inline int64_t wofs(int l, int C) { return l == 0 ? 0 : 9LL * C + (int64_t)(l - 1) * 9 * C * C; }
 
-// ---------------------------------------------------------------- forward conv
-// out[n][co][y][x] = act(b[co] + sum_ci,ky,kx w[co][ci][ky][kx] in[n][ci][y+ky-1][x+kx-1])
-// Layer 0 reads X = l_{k+1} - l_k from the clip's log frames: image n is
-// (clip b = n / nseg, step k = k0 + n % nseg).  The last layer also writes the
-// projection I = bp + wp . a.
-template <bool kFromLogl>
+// ------------------------------------------------------ forward conv, layer 0
+// out[n][co][y][x] = ReLU(b[co] + sum_ky,kx w[co][ky][kx] X[n][y+ky-1][x+kx-1]), X read as
+// l_{k+1} - l_k from the clip's log frames: image n is (clip b = n / nseg, step
+// k = k0 + n % nseg).  A one-layer network also writes the projection I = bp + wp . a.
 __global__ void __launch_bounds__(TS * TS)
-conv_fwd(const float* __restrict__ in, const float* __restrict__ logl, int K, int k0, int nseg,
-         int Cin, int C, int H, int W, const float* __restrict__ w, const float* __restrict__ b,
-         float* __restrict__ out, const float* __restrict__ wp, const float* __restrict__ bp,
-         float* __restrict__ I) {
+conv_fwd(const float* __restrict__ logl, int K, int k0, int nseg, int C, int H, int W,
+         const float* __restrict__ w, const float* __restrict__ b, float* __restrict__ out,
+         const float* __restrict__ wp, const float* __restrict__ bp, float* __restrict__ I) {
+  constexpr int Cin = 1;
   __shared__ float tin[kMaxC][TS + 2][TS + 2];
   __shared__ float tw[kMaxC * kMaxC * 9];
   const int n = blockIdx.z;
@@ -60,13 +58,9 @@ conv_fwd(const float* __restrict__ in, const float* __restrict__ logl, int K, in
     float v = 0.0f;
     if (yy >= 0 && yy < H && xx >= 0 && xx < W) {
       const int64_t g = (int64_t)yy * W + xx;
-      if (kFromLogl) {
-        const int bc = n / nseg, k = k0 + n % nseg;
-        const float* lf = logl + (int64_t)bc * (K + 1) * hw;
-        v = lf[(int64_t)(k + 1) * hw + g] - lf[(int64_t)k * hw + g];
-      } else {
-        v = in[((int64_t)n * Cin + ci) * hw + g];
-      }
+      const int bc = n / nseg, k = k0 + n % nseg;
+      const float* lf = logl + (int64_t)bc * (K + 1) * hw;
+      v = lf[(int64_t)(k + 1) * hw + g] - lf[(int64_t)k * hw + g];
     }
     tin[ci][r / (TS + 2)][r % (TS + 2)] = v;
   }
@@ -187,52 +181,14 @@ proj_bwd(const float* __restrict__ dI, const float* __restrict__ a, int N, int C
   }
 }
 
-// ------------------------------------------------------- conv data backward
-// dzp[n][ci][y][x] = (sum_co,ky,kx w[co][ci][ky][kx] dz[n][co][y-ky+1][x-kx+1]) 1(a_prev > 0)
+// ------------------------------------------------ conv weight backward, layer 0
+// grad w[co][t] += sum_n,y,x dz[n][co][y][x] X[n][y+ky-1][x+kx-1] (X from the log
+// frames as in the forward); grad b[co] += sum dz.  Persistent blocks
+// accumulate over many tiles in registers, then one atomic per entry per block.
 __global__ void __launch_bounds__(TS * TS)
-conv_bwd_data(const float* __restrict__ dz, int Cin, int C, int H, int W,
-              const float* __restrict__ w, const float* __restrict__ a_prev,
-              float* __restrict__ dzp) {
-  __shared__ float td[kMaxC][TS + 2][TS + 2];
-  __shared__ float tw[kMaxC * kMaxC * 9];
-  const int n = blockIdx.z;
-  const int tx = threadIdx.x % TS, ty = threadIdx.x / TS;
-  const int x0 = blockIdx.x * TS, y0 = blockIdx.y * TS;
-  const int64_t hw = (int64_t)H * W;
-  for (int i = threadIdx.x; i < C * Cin * 9; i += TS * TS) tw[i] = w[i];
-  for (int i = threadIdx.x; i < C * (TS + 2) * (TS + 2); i += TS * TS) {
-    const int co = i / ((TS + 2) * (TS + 2)), r = i % ((TS + 2) * (TS + 2));
-    const int yy = y0 - 1 + r / (TS + 2), xx = x0 - 1 + r % (TS + 2);
-    td[co][r / (TS + 2)][r % (TS + 2)] =
-        (yy >= 0 && yy < H && xx >= 0 && xx < W) ? dz[((int64_t)n * C + co) * hw + (int64_t)yy * W + xx] : 0.0f;
-  }
-  __syncthreads();
-  const int x = x0 + tx, y = y0 + ty;
-  if (x >= W || y >= H) return;
-  for (int ci = 0; ci < Cin; ++ci) {
-    float acc = 0.0f;
-    for (int co = 0; co < C; ++co) {
-      const float* wr = tw + (co * Cin + ci) * 9;
-#pragma unroll
-      for (int t = 0; t < 9; ++t) {
-        // output (y + 1 - ky, x + 1 - kx) used input (y, x) through tap (ky, kx)
-        acc += wr[t] * td[co][ty + 2 - t / 3][tx + 2 - t % 3];
-      }
-    }
-    const int64_t o = ((int64_t)n * Cin + ci) * hw + (int64_t)y * W + x;
-    dzp[o] = a_prev[o] > 0.0f ? acc : 0.0f;
-  }
-}
-
-// ----------------------------------------------------- conv weight backward
-// grad w[co][ci][t] += sum_n,y,x dz[n][co][y][x] in[n][ci][y+ky-1][x+kx-1];
-// grad b[co] += sum dz.  Persistent blocks accumulate over many tiles in
-// registers, then one atomic per entry per block.
-template <bool kFromLogl>
-__global__ void __launch_bounds__(TS * TS)
-conv_bwd_weight(const float* __restrict__ dz, const float* __restrict__ in,
-                const float* __restrict__ logl, int K, int k0, int nseg, int N, int Cin, int C,
-                int H, int W, float* __restrict__ gw, float* __restrict__ gb) {
+conv_bwd_weight(const float* __restrict__ dz, const float* __restrict__ logl, int K, int k0,
+                int nseg, int N, int C, int H, int W, float* __restrict__ gw, float* __restrict__ gb) {
+  constexpr int Cin = 1;
   __shared__ float td[kMaxC][TS][TS];
   __shared__ float tin[kMaxC][TS + 2][TS + 2];
   constexpr int kPer = (kMaxC * kMaxC * 9 + kMaxC + TS * TS - 1) / (TS * TS);
@@ -259,13 +215,9 @@ conv_bwd_weight(const float* __restrict__ dz, const float* __restrict__ in,
       float v = 0.0f;
       if (yy >= 0 && yy < H && xx >= 0 && xx < W) {
         const int64_t g = (int64_t)yy * W + xx;
-        if (kFromLogl) {
-          const int bc = n / nseg, k = k0 + n % nseg;
-          const float* lf = logl + (int64_t)bc * (K + 1) * hw;
-          v = lf[(int64_t)(k + 1) * hw + g] - lf[(int64_t)k * hw + g];
-        } else {
-          v = in[((int64_t)n * Cin + ci) * hw + g];
-        }
+        const int bc = n / nseg, k = k0 + n % nseg;
+        const float* lf = logl + (int64_t)bc * (K + 1) * hw;
+        v = lf[(int64_t)(k + 1) * hw + g] - lf[(int64_t)k * hw + g];
       }
       tin[ci][r / (TS + 2)][r % (TS + 2)] = v;
     }
@@ -294,6 +246,228 @@ conv_bwd_weight(const float* __restrict__ dz, const float* __restrict__ in,
     if (e >= nent) break;
     if (e < C * Cin * 9) atomicAdd(gw + e, acc[j]);
     else atomicAdd(gb + (e - C * Cin * 9), acc[j]);
+  }
+}
+
+// ------------------------------------------- C -> C layers, register-blocked
+// The layers with C input channels (all but the first) in a second form: the
+// 16 x 16 tile (+ halo) of all channels is staged channel-interleaved in shared
+// memory, 16 floats per position, the four 16-byte groups of position m
+// permuted by (m >> 1) & 3 so that eight consecutive positions read a group
+// from eight different bank quads.  Channels are zero-padded to 16.
+constexpr int CP = 16;
+constexpr int TP = TS + 2;     // tile with halo
+
+__device__ __forceinline__ int cidx(int m, int g) { return m * CP + 4 * (g ^ ((m >> 1) & 3)); }
+
+// plane-major [c][y][x] tile (rows y0 - h .., columns x0 - h .., tw x th) ->
+// interleaved shared memory; zero outside the image and for c >= C
+__device__ __forceinline__ void stage(float* __restrict__ s, const float* __restrict__ g, int C,
+                                      int H, int W, int x0, int y0, int h, int tw, int th) {
+  const int64_t hw = (int64_t)H * W;
+  for (int i = threadIdx.x; i < CP * tw * th; i += blockDim.x) {
+    const int c = i / (tw * th), r = i % (tw * th);
+    const int yy = y0 - h + r / tw, xx = x0 - h + r % tw;
+    float v = 0.0f;
+    if (c < C && yy >= 0 && yy < H && xx >= 0 && xx < W) v = g[(int64_t)c * hw + (int64_t)yy * W + xx];
+    s[cidx(r, c >> 2) + (c & 3)] = v;
+  }
+}
+
+// acc[k][c] += sum over taps t and input channels of wt[t][ci][4 cg + c] x[m_k + off(t)][ci]
+// (off(t) = (t / 3 - 1, t % 3 - 1) on a TP-wide tile); 4 positions x 4 channels
+// per thread, 8 vector loads per 64 FMAs
+__device__ __forceinline__ void conv_block(const float* __restrict__ sx, const float* __restrict__ wt,
+                                           const int (&m)[4], int cg, float (&acc)[4][4]) {
+#pragma unroll 1
+  for (int t = 0; t < 9; ++t) {
+    const int toff = (t / 3 - 1) * TP + (t % 3 - 1);
+    const float* w = wt + t * CP * CP + 4 * cg;
+    int mk[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) mk[k] = m[k] + toff;
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      const float4 wa = *reinterpret_cast<const float4*>(w + (4 * g + 0) * CP);
+      const float4 wb = *reinterpret_cast<const float4*>(w + (4 * g + 1) * CP);
+      const float4 wc = *reinterpret_cast<const float4*>(w + (4 * g + 2) * CP);
+      const float4 wd = *reinterpret_cast<const float4*>(w + (4 * g + 3) * CP);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float4 x = *reinterpret_cast<const float4*>(sx + cidx(mk[k], g));
+        acc[k][0] = fmaf(wa.x, x.x, acc[k][0]); acc[k][1] = fmaf(wa.y, x.x, acc[k][1]);
+        acc[k][2] = fmaf(wa.z, x.x, acc[k][2]); acc[k][3] = fmaf(wa.w, x.x, acc[k][3]);
+        acc[k][0] = fmaf(wb.x, x.y, acc[k][0]); acc[k][1] = fmaf(wb.y, x.y, acc[k][1]);
+        acc[k][2] = fmaf(wb.z, x.y, acc[k][2]); acc[k][3] = fmaf(wb.w, x.y, acc[k][3]);
+        acc[k][0] = fmaf(wc.x, x.z, acc[k][0]); acc[k][1] = fmaf(wc.y, x.z, acc[k][1]);
+        acc[k][2] = fmaf(wc.z, x.z, acc[k][2]); acc[k][3] = fmaf(wc.w, x.z, acc[k][3]);
+        acc[k][0] = fmaf(wd.x, x.w, acc[k][0]); acc[k][1] = fmaf(wd.y, x.w, acc[k][1]);
+        acc[k][2] = fmaf(wd.z, x.w, acc[k][2]); acc[k][3] = fmaf(wd.w, x.w, acc[k][3]);
+      }
+    }
+  }
+}
+
+// Thread layout of the 256-thread blocks below: warp w, lane (pg = lane / 4,
+// cg = lane % 4) computes channels 4 cg .. 4 cg + 3 at the tile positions
+// w * 32 + k * 8 + pg, k = 0..3.
+__device__ __forceinline__ void tile_positions(int (&pix)[4], int (&m)[4]) {
+  const int warp = threadIdx.x >> 5, pg = (threadIdx.x & 31) >> 2;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    pix[k] = warp * 32 + k * 8 + pg;
+    m[k] = (pix[k] / TS + 1) * TP + pix[k] % TS + 1;
+  }
+}
+
+// forward: out = ReLU(b + conv(in)); the last layer also I = bp + wp . out
+__global__ void __launch_bounds__(TS * TS)
+conv16_fwd(const float* __restrict__ in, int C, int H, int W, const float* __restrict__ w,
+           const float* __restrict__ b, float* __restrict__ out, const float* __restrict__ wp,
+           const float* __restrict__ bp, float* __restrict__ I) {
+  __shared__ __align__(16) float sx[TP * TP * CP];
+  __shared__ __align__(16) float sw[9 * CP * CP];    // [t][ci][co]
+  __shared__ __align__(16) float sb[CP], swp[CP];
+  const int n = blockIdx.z, x0 = blockIdx.x * TS, y0 = blockIdx.y * TS;
+  const int64_t hw = (int64_t)H * W;
+  for (int i = threadIdx.x; i < 9 * CP * CP; i += TS * TS) {
+    const int co = i % CP, ci = (i / CP) % CP, t = i / (CP * CP);
+    sw[i] = (co < C && ci < C) ? w[(co * C + ci) * 9 + t] : 0.0f;
+  }
+  if (threadIdx.x < CP) {
+    sb[threadIdx.x] = threadIdx.x < C ? b[threadIdx.x] : 0.0f;
+    swp[threadIdx.x] = (I && threadIdx.x < C) ? wp[threadIdx.x] : 0.0f;
+  }
+  stage(sx, in + (int64_t)n * C * hw, C, H, W, x0, y0, 1, TP, TP);
+  __syncthreads();
+  const int cg = threadIdx.x & 3;
+  int pix[4], m[4];
+  tile_positions(pix, m);
+  float acc[4][4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[k][c] = sb[4 * cg + c];
+  conv_block(sx, sw, m, cg, acc);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int x = x0 + pix[k] % TS, y = y0 + pix[k] / TS;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      acc[k][c] = fmaxf(acc[k][c], 0.0f);
+      if (x < W && y < H && 4 * cg + c < C)
+        out[((int64_t)n * C + 4 * cg + c) * hw + (int64_t)y * W + x] = acc[k][c];
+    }
+  }
+  if (I) {
+    // Eq. 6: the 4 channel lanes of a position sum their parts; lane cg writes position cg
+    float mine = 0.0f;
+    int pmine = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      float s = swp[4 * cg] * acc[k][0];
+      s = fmaf(swp[4 * cg + 1], acc[k][1], s);
+      s = fmaf(swp[4 * cg + 2], acc[k][2], s);
+      s = fmaf(swp[4 * cg + 3], acc[k][3], s);
+      s += __shfl_xor_sync(0xFFFFFFFFu, s, 1);
+      s += __shfl_xor_sync(0xFFFFFFFFu, s, 2);
+      if (k == cg) { mine = s; pmine = pix[k]; }
+    }
+    const int x = x0 + pmine % TS, y = y0 + pmine / TS;
+    if (x < W && y < H) I[(int64_t)n * hw + (int64_t)y * W + x] = bp[0] + mine;
+  }
+}
+
+// data backward: dzp[ci] = (sum_co,t w[co][ci][t] dz[co] at the mirrored tap) 1(a_prev > 0),
+// i.e. the forward block with weights w'[t][co][ci] = w[co][ci][8 - t]
+__global__ void __launch_bounds__(TS * TS)
+conv16_bwd_data(const float* __restrict__ dz, int C, int H, int W, const float* __restrict__ w,
+                const float* __restrict__ a_prev, float* __restrict__ dzp) {
+  __shared__ __align__(16) float sx[TP * TP * CP];
+  __shared__ __align__(16) float sw[9 * CP * CP];    // [t][co][ci]
+  const int n = blockIdx.z, x0 = blockIdx.x * TS, y0 = blockIdx.y * TS;
+  const int64_t hw = (int64_t)H * W;
+  for (int i = threadIdx.x; i < 9 * CP * CP; i += TS * TS) {
+    const int ci = i % CP, co = (i / CP) % CP, t = i / (CP * CP);
+    sw[i] = (co < C && ci < C) ? w[(co * C + ci) * 9 + (8 - t)] : 0.0f;
+  }
+  stage(sx, dz + (int64_t)n * C * hw, C, H, W, x0, y0, 1, TP, TP);
+  __syncthreads();
+  const int cg = threadIdx.x & 3;
+  int pix[4], m[4];
+  tile_positions(pix, m);
+  float acc[4][4] = {};
+  conv_block(sx, sw, m, cg, acc);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int x = x0 + pix[k] % TS, y = y0 + pix[k] / TS;
+    if (x >= W || y >= H) continue;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      if (4 * cg + c >= C) continue;
+      const int64_t o = ((int64_t)n * C + 4 * cg + c) * hw + (int64_t)y * W + x;
+      dzp[o] = a_prev[o] > 0.0f ? acc[k][c] : 0.0f;
+    }
+  }
+}
+
+// weight backward: grad w[co][ci][t] += sum_n,p dz[n][co][p] in[n][ci][p + off(t)],
+// grad b[co] += sum dz.  Persistent blocks of 160 threads: thread e < 144 owns
+// (tap t = e / 16, output quad e % 4, input quad (e / 4) % 4), 16 sums; threads
+// 144..159 own the bias sums of one output channel each.  One atomic per entry
+// per block at the end.
+constexpr int kWThreads = 160;
+__global__ void __launch_bounds__(kWThreads)
+conv16_bwd_weight(const float* __restrict__ dz, const float* __restrict__ in, int N, int C, int H,
+                  int W, float* __restrict__ gw, float* __restrict__ gb) {
+  __shared__ __align__(16) float sd[TS * TS * CP];
+  __shared__ __align__(16) float sx[TP * TP * CP];
+  const int e = threadIdx.x;
+  const int t = e / 16, cq = e % 4, iq = (e / 4) % 4;
+  const int toff = (t / 3) * TP + t % 3;          // tap offset from the tile position's halo corner
+  float acc[4][4] = {};
+  float bsum = 0.0f;
+  const int64_t hw = (int64_t)H * W;
+  const int tiles_x = (W + TS - 1) / TS, tiles_y = (H + TS - 1) / TS;
+  const int64_t ntiles = (int64_t)N * tiles_x * tiles_y;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int n = (int)(tile / (tiles_x * tiles_y));
+    const int tt = (int)(tile % (tiles_x * tiles_y));
+    const int x0 = (tt % tiles_x) * TS, y0 = (tt / tiles_x) * TS;
+    __syncthreads();
+    stage(sd, dz + (int64_t)n * C * hw, C, H, W, x0, y0, 0, TS, TS);
+    stage(sx, in + (int64_t)n * C * hw, C, H, W, x0, y0, 1, TP, TP);
+    __syncthreads();
+    if (e < 144) {
+#pragma unroll 2
+      for (int py = 0; py < TS; ++py) {
+#pragma unroll 4
+        for (int px = 0; px < TS; ++px) {
+          const int p = py * TS + px, q = py * TP + px + toff;
+          const float4 d = *reinterpret_cast<const float4*>(sd + cidx(p, cq));
+          const float4 x = *reinterpret_cast<const float4*>(sx + cidx(q, iq));
+          const float dv[4] = {d.x, d.y, d.z, d.w}, xv[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[a][c] = fmaf(dv[a], xv[c], acc[a][c]);
+        }
+      }
+    } else {
+      const int co = e - 144;
+      for (int p = 0; p < TS * TS; ++p) bsum += sd[cidx(p, co >> 2) + (co & 3)];
+    }
+  }
+  if (e < 144) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int co = 4 * cq + a, ci = 4 * iq + c;
+        if (co < C && ci < C) atomicAdd(gw + (co * C + ci) * 9 + t, acc[a][c]);
+      }
+  } else if (e - 144 < C) {
+    atomicAdd(gb + (e - 144), bsum);
   }
 }
 
@@ -446,12 +620,12 @@ int seg_forward(const float* logl, const et_train_shape* sh, const et_evsnet_wei
   for (int l = 0; l < L; ++l) {
     const bool last = l == L - 1;
     if (l == 0)
-      conv_fwd<true><<<grid, TS * TS, 0, st>>>(nullptr, logl, sh->K, k0, nseg, 1, C, H, W, net->w,
-                                               net->b, ws.act[0], wproj, bproj, last ? ws.I : nullptr);
+      conv_fwd<<<grid, TS * TS, 0, st>>>(logl, sh->K, k0, nseg, C, H, W, net->w, net->b, ws.act[0],
+                                         wproj, bproj, last ? ws.I : nullptr);
     else
-      conv_fwd<false><<<grid, TS * TS, 0, st>>>(ws.act[l - 1], nullptr, sh->K, k0, nseg, C, C, H, W,
-                                                net->w + wofs(l, C), net->b + (int64_t)l * C, ws.act[l],
-                                                wproj, bproj, last ? ws.I : nullptr);
+      conv16_fwd<<<grid, TS * TS, 0, st>>>(ws.act[l - 1], C, H, W, net->w + wofs(l, C),
+                                           net->b + (int64_t)l * C, ws.act[l], wproj, bproj,
+                                           last ? ws.I : nullptr);
     ET_CHECK_LAUNCH();
   }
   return ET_OK;
@@ -546,6 +720,9 @@ extern "C" int et_evsnet_train_backward(const float* logl, const et_train_shape*
   int dev = 0, nsm = 0;
   ET_CHECK_CUDA(cudaGetDevice(&dev));
   ET_CHECK_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  int wblocks = 0;   // resident weight-gradient blocks per SM: one wave of persistent blocks
+  ET_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&wblocks, conv16_bwd_weight, kWThreads, 0));
+  wblocks = std::max(wblocks, 1);
   ET_CHECK_CUDA(cudaMemsetAsync(ws.V, 0, sizeof(float) * sh->B * hw, st));   // dL/dV after the last step
   float* gwp = grad_w + wofs(L, C);
   float* gbp = grad_b + (int64_t)L * C;
@@ -565,18 +742,16 @@ extern "C" int et_evsnet_train_backward(const float* logl, const et_train_shape*
     dim3 grid((W + TS - 1) / TS, (H + TS - 1) / TS, N);
     int cur = 0;
     for (int l = L - 1; l >= 0; --l) {
-      const int cin = l == 0 ? 1 : C;
       if (l == 0)
-        conv_bwd_weight<true><<<nsm * 2, TS * TS, 0, st>>>(ws.dz[cur], nullptr, logl, sh->K, k0, nseg, N,
-                                                           1, C, H, W, grad_w + wofs(0, C), grad_b);
+        conv_bwd_weight<<<nsm * 2, TS * TS, 0, st>>>(ws.dz[cur], logl, sh->K, k0, nseg, N, C, H, W,
+                                                     grad_w + wofs(0, C), grad_b);
       else
-        conv_bwd_weight<false><<<nsm * 2, TS * TS, 0, st>>>(ws.dz[cur], ws.act[l - 1], nullptr, sh->K, k0,
-                                                            nseg, N, C, C, H, W, grad_w + wofs(l, C),
-                                                            grad_b + (int64_t)l * C);
+        conv16_bwd_weight<<<nsm * wblocks, kWThreads, 0, st>>>(ws.dz[cur], ws.act[l - 1], N, C, H, W,
+                                                               grad_w + wofs(l, C), grad_b + (int64_t)l * C);
       ET_CHECK_LAUNCH();
       if (l > 0) {
-        conv_bwd_data<<<grid, TS * TS, 0, st>>>(ws.dz[cur], cin, C, H, W, net->w + wofs(l, C),
-                                                ws.act[l - 1], ws.dz[cur ^ 1]);
+        conv16_bwd_data<<<grid, TS * TS, 0, st>>>(ws.dz[cur], C, H, W, net->w + wofs(l, C),
+                                                  ws.act[l - 1], ws.dz[cur ^ 1]);
         ET_CHECK_LAUNCH();
         cur ^= 1;
       }
