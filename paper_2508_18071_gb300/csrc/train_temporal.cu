@@ -28,15 +28,14 @@ __host__ __device__ inline int64_t twofs(int l, int C, int kt) {
   return l == 0 ? 0 : (int64_t)C * kt + (int64_t)(l - 1) * C * C * kt;
 }
 
-// --------------------------------------------------------------- forward conv
-// One thread per (clip, step, pixel).  res (optional) is added before the ReLU;
-// the last layer also writes the projection I = bp + wp . out.
-template <bool kFromLogl>
-__global__ void __launch_bounds__(256)
-tconv_fwd(const float* __restrict__ in, const float* __restrict__ logl, int B, int K, int64_t hw,
-          int Cin, int C, int kt, const float* __restrict__ w, const float* __restrict__ b,
-          const float* __restrict__ res, float* __restrict__ out, const float* __restrict__ wp,
-          const float* __restrict__ bp, float* __restrict__ I) {
+// ------------------------------------------------------- forward conv, layer 0
+// One thread per (clip, step, pixel); X read as l_{k+1} - l_k from the clip's
+// log frames.  A one-layer network also writes the projection I = bp + wp . out.
+__global__ void __launch_bounds__(256, 4)
+tconv_fwd(const float* __restrict__ logl, int B, int K, int64_t hw, int C, int kt,
+          const float* __restrict__ w, const float* __restrict__ b, float* __restrict__ out,
+          const float* __restrict__ wp, const float* __restrict__ bp, float* __restrict__ I) {
+  constexpr int Cin = 1;
   __shared__ float sw[kMaxC * kMaxC * kMaxKt];
   for (int i = threadIdx.x; i < C * Cin * kt; i += blockDim.x) sw[i] = w[i];
   __syncthreads();
@@ -50,29 +49,18 @@ tconv_fwd(const float* __restrict__ in, const float* __restrict__ logl, int B, i
   for (int tau = 0; tau < kt; ++tau) {
     const int kk = k - (kt - 1) + tau;
     if (kk < 0) continue;
-    if (kFromLogl) {
-      const float* lf = logl + (int64_t)bc * (K + 1) * hw;
-      const float x = lf[(int64_t)(kk + 1) * hw + p] - lf[(int64_t)kk * hw + p];
+    const float* lf = logl + (int64_t)bc * (K + 1) * hw;
+    const float x = lf[(int64_t)(kk + 1) * hw + p] - lf[(int64_t)kk * hw + p];
 #pragma unroll
-      for (int co = 0; co < kMaxC; ++co)
-        if (co < C) acc[co] += sw[co * kt + tau] * x;
-    } else {
-      const float* src = in + (((int64_t)bc * K + kk) * hw + p) * Cin;
-      for (int ci = 0; ci < Cin; ++ci) {
-        const float x = src[ci];
-#pragma unroll
-        for (int co = 0; co < kMaxC; ++co)
-          if (co < C) acc[co] += sw[(co * Cin + ci) * kt + tau] * x;
-      }
-    }
+    for (int co = 0; co < kMaxC; ++co)
+      if (co < C) acc[co] += sw[co * kt + tau] * x;
   }
   float* dst = out + idx * C;
   float Iv = bp ? bp[0] : 0.0f;
 #pragma unroll
   for (int co = 0; co < kMaxC; ++co) {
     if (co >= C) break;
-    const float z = res ? acc[co] + res[idx * C + co] : acc[co];
-    const float a = fmaxf(z, 0.0f);
+    const float a = fmaxf(acc[co], 0.0f);
     dst[co] = a;
     if (I) Iv += wp[co] * a;
   }
@@ -178,52 +166,15 @@ tproj_bwd(const float* __restrict__ dI, const float* __restrict__ h, int64_t n, 
   }
 }
 
-// ---------------------------------------------------------- data backward
-// out[s][ci] = (add[s][ci] + sum_tau,co w[co][ci][tau] dz[s + kt - 1 - tau][co]) 1(mask[s][ci] > 0)
-__global__ void __launch_bounds__(256)
-tconv_bwd_data(const float* __restrict__ dz, int B, int K, int64_t hw, int Cin, int C, int kt,
-               const float* __restrict__ w, const float* __restrict__ add,
-               const float* __restrict__ mask, float* __restrict__ out) {
-  __shared__ float sw[kMaxC * kMaxC * kMaxKt];
-  for (int i = threadIdx.x; i < C * Cin * kt; i += blockDim.x) sw[i] = w[i];
-  __syncthreads();
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)B * K * hw) return;
-  const int64_t p = idx % hw;
-  const int s = (int)((idx / hw) % K), bc = (int)(idx / (hw * K));
-  float acc[kMaxC];
-#pragma unroll
-  for (int ci = 0; ci < kMaxC; ++ci) acc[ci] = 0.0f;
-  for (int tau = 0; tau < kt; ++tau) {
-    const int k = s + kt - 1 - tau;
-    if (k >= K) continue;
-    const float* d = dz + (((int64_t)bc * K + k) * hw + p) * C;
-    for (int co = 0; co < C; ++co) {
-      const float g = d[co];
-#pragma unroll
-      for (int ci = 0; ci < kMaxC; ++ci)
-        if (ci < Cin) acc[ci] += sw[(co * Cin + ci) * kt + tau] * g;
-    }
-  }
-#pragma unroll
-  for (int ci = 0; ci < kMaxC; ++ci) {
-    if (ci >= Cin) break;
-    const int64_t o = idx * Cin + ci;
-    const float v = add ? add[o] + acc[ci] : acc[ci];
-    out[o] = mask[o] > 0.0f ? v : 0.0f;
-  }
-}
-
-// -------------------------------------------------------- weight backward
-// grad w[co][ci][tau] += sum dz[k][co] in[k - kt + 1 + tau][ci]; grad b[co] += sum dz[k][co].
+// ------------------------------------------------- weight backward, layer 0
+// grad w[co][tau] += sum dz[k][co] X[k - kt + 1 + tau]; grad b[co] += sum dz[k][co].
 // Persistent blocks stage 32 pixel-steps at a time in shared memory; each
-// thread owns a few (co, ci, tau) entries, one atomic per entry per block.
+// thread owns a few (co, tau) entries, one atomic per entry per block.
 constexpr int kPts = 32;
-template <bool kFromLogl>
 __global__ void __launch_bounds__(256)
-tconv_bwd_weight(const float* __restrict__ dz, const float* __restrict__ in,
-                 const float* __restrict__ logl, int B, int K, int64_t hw, int Cin, int C, int kt,
-                 float* __restrict__ gw, float* __restrict__ gb) {
+tconv_bwd_weight(const float* __restrict__ dz, const float* __restrict__ logl, int B, int K,
+                 int64_t hw, int C, int kt, float* __restrict__ gw, float* __restrict__ gb) {
+  constexpr int Cin = 1;
   __shared__ float sd[kPts][kMaxC];
   __shared__ float sx[kPts][kMaxC * kMaxKt + 1];   // [ci][tau], padded
   constexpr int kPer = (kMaxC * kMaxC * kMaxKt + kMaxC + 255) / 256;
@@ -248,12 +199,8 @@ tconv_bwd_weight(const float* __restrict__ dz, const float* __restrict__ in,
         const int k = (int)((idx / hw) % K), bc = (int)(idx / (hw * K));
         const int kk = k - (kt - 1) + tau;
         if (kk >= 0) {
-          if (kFromLogl) {
-            const float* lf = logl + (int64_t)bc * (K + 1) * hw;
-            v = lf[(int64_t)(kk + 1) * hw + p] - lf[(int64_t)kk * hw + p];
-          } else {
-            v = in[(((int64_t)bc * K + kk) * hw + p) * Cin + ci];
-          }
+          const float* lf = logl + (int64_t)bc * (K + 1) * hw;
+          v = lf[(int64_t)(kk + 1) * hw + p] - lf[(int64_t)kk * hw + p];
         }
       }
       sx[pt][ci * kt + tau] = v;
@@ -280,6 +227,199 @@ tconv_bwd_weight(const float* __restrict__ dz, const float* __restrict__ in,
     if (e >= nent) break;
     if (e < C * Cin * kt) atomicAdd(gw + e, acc[j]);
     else atomicAdd(gb + (e - C * Cin * kt), acc[j]);
+  }
+}
+
+// ------------------------------------------- C -> C layers, vectorised weights
+// The layers with C input channels in a second form: weights staged as
+// [tau][input][output], zero-padded to 16 x 16 per tap, so that one 16-byte
+// shared load (the same address for the whole warp) feeds four FMAs; a
+// pixel-step's 16 channels are read with 16-byte loads when C = 16.
+constexpr int CP = 16;
+
+template <bool kC16>
+__device__ __forceinline__ void load_ch(const float* __restrict__ src, int C, float (&x)[CP]) {
+  if (kC16) {
+#pragma unroll
+    for (int j = 0; j < CP / 4; ++j) {
+      const float4 v = __ldg(reinterpret_cast<const float4*>(src) + j);
+      x[4 * j] = v.x; x[4 * j + 1] = v.y; x[4 * j + 2] = v.z; x[4 * j + 3] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < CP; ++c) x[c] = c < C ? __ldg(src + c) : 0.0f;
+  }
+}
+
+// acc[o] += sum_i w[i][o] x[i] for one tap's 16 x 16 block of shared weights
+__device__ __forceinline__ void fma_block(const float* __restrict__ w, const float (&x)[CP], int C,
+                                          float (&acc)[CP]) {
+#pragma unroll
+  for (int i = 0; i < CP; ++i) {
+    if (i >= C) break;
+    const float4* w4 = reinterpret_cast<const float4*>(w + i * CP);
+#pragma unroll
+    for (int j = 0; j < CP / 4; ++j) {
+      const float4 v = w4[j];
+      acc[4 * j] = fmaf(v.x, x[i], acc[4 * j]);
+      acc[4 * j + 1] = fmaf(v.y, x[i], acc[4 * j + 1]);
+      acc[4 * j + 2] = fmaf(v.z, x[i], acc[4 * j + 2]);
+      acc[4 * j + 3] = fmaf(v.w, x[i], acc[4 * j + 3]);
+    }
+  }
+}
+
+// forward of a C -> C layer: out = ReLU(b + conv(in) [+ res]), the last layer
+// also I = bp + wp . out; one thread per (clip, step, pixel)
+template <bool kC16>
+__global__ void __launch_bounds__(256, 4)
+tconv16_fwd(const float* __restrict__ in, int B, int K, int64_t hw, int C, int kt,
+            const float* __restrict__ w, const float* __restrict__ b, const float* __restrict__ res,
+            float* __restrict__ out, const float* __restrict__ wp, const float* __restrict__ bp,
+            float* __restrict__ I) {
+  __shared__ __align__(16) float sw[kMaxKt * CP * CP];   // [tau][ci][co]
+  for (int i = threadIdx.x; i < kt * CP * CP; i += blockDim.x) {
+    const int co = i % CP, ci = (i / CP) % CP, tau = i / (CP * CP);
+    sw[i] = (co < C && ci < C) ? w[(co * C + ci) * kt + tau] : 0.0f;
+  }
+  __syncthreads();
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)B * K * hw) return;
+  const int64_t p = idx % hw;
+  const int k = (int)((idx / hw) % K), bc = (int)(idx / (hw * K));
+  float acc[CP];
+#pragma unroll
+  for (int co = 0; co < CP; ++co) acc[co] = co < C ? b[co] : 0.0f;
+  for (int tau = 0; tau < kt; ++tau) {
+    const int kk = k - (kt - 1) + tau;
+    if (kk < 0) continue;
+    float x[CP];
+    load_ch<kC16>(in + (((int64_t)bc * K + kk) * hw + p) * C, C, x);
+    fma_block(sw + tau * CP * CP, x, C, acc);
+  }
+  float Iv = bp ? bp[0] : 0.0f;
+#pragma unroll
+  for (int co = 0; co < CP; ++co) {
+    if (co >= C) break;
+    const float z = res ? acc[co] + res[idx * C + co] : acc[co];
+    acc[co] = fmaxf(z, 0.0f);
+    if (I) Iv += wp[co] * acc[co];
+  }
+  if (kC16) {
+#pragma unroll
+    for (int j = 0; j < CP / 4; ++j)
+      reinterpret_cast<float4*>(out + idx * C)[j] =
+          make_float4(acc[4 * j], acc[4 * j + 1], acc[4 * j + 2], acc[4 * j + 3]);
+  } else {
+#pragma unroll
+    for (int co = 0; co < CP; ++co)
+      if (co < C) out[idx * C + co] = acc[co];
+  }
+  if (I) I[idx] = Iv;
+}
+
+// data backward: out[s][ci] = (add[s][ci] + sum_tau,co w[co][ci][tau] dz[s + kt - 1 - tau][co])
+// 1(mask[s][ci] > 0); weights staged [tau][co][ci]
+template <bool kC16>
+__global__ void __launch_bounds__(256, 4)
+tconv16_bwd_data(const float* __restrict__ dz, int B, int K, int64_t hw, int C, int kt,
+                 const float* __restrict__ w, const float* __restrict__ add,
+                 const float* __restrict__ mask, float* __restrict__ out) {
+  __shared__ __align__(16) float sw[kMaxKt * CP * CP];   // [tau][co][ci]
+  for (int i = threadIdx.x; i < kt * CP * CP; i += blockDim.x) {
+    const int ci = i % CP, co = (i / CP) % CP, tau = i / (CP * CP);
+    sw[i] = (co < C && ci < C) ? w[(co * C + ci) * kt + tau] : 0.0f;
+  }
+  __syncthreads();
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)B * K * hw) return;
+  const int64_t p = idx % hw;
+  const int s = (int)((idx / hw) % K), bc = (int)(idx / (hw * K));
+  float acc[CP];
+#pragma unroll
+  for (int ci = 0; ci < CP; ++ci) acc[ci] = 0.0f;
+  for (int tau = 0; tau < kt; ++tau) {
+    const int k = s + kt - 1 - tau;
+    if (k >= K) continue;
+    float g[CP];
+    load_ch<kC16>(dz + (((int64_t)bc * K + k) * hw + p) * C, C, g);
+    fma_block(sw + tau * CP * CP, g, C, acc);
+  }
+#pragma unroll
+  for (int ci = 0; ci < CP; ++ci) {
+    if (ci >= C) break;
+    const int64_t o = idx * C + ci;
+    const float v = add ? add[o] + acc[ci] : acc[ci];
+    out[o] = mask[o] > 0.0f ? v : 0.0f;
+  }
+}
+
+// weight backward of a C -> C layer: grad w[co][ci][tau] += sum dz[k][co] in[k - kt + 1 + tau][ci],
+// grad b[co] += sum dz[k][co].  Persistent blocks stage kPts16 pixel-steps:
+// dz as [pt][16], the shifted inputs as [pt][tau][16].  Thread e < 16 kt owns
+// (tap tau = e / 16, output quad e % 4, input quad (e / 4) % 4), 16 sums with
+// two 16-byte shared loads per 16 FMAs; the next 16 threads own the bias sums.
+constexpr int kPts16 = 64;
+inline int twgrad_threads(int kt) { return (16 * kt + 16 + 31) / 32 * 32; }
+
+template <bool kC16>
+__global__ void __launch_bounds__(320)
+tconv16_bwd_weight(const float* __restrict__ dz, const float* __restrict__ in, int B, int K,
+                   int64_t hw, int C, int kt, float* __restrict__ gw, float* __restrict__ gb) {
+  extern __shared__ __align__(16) float tsm[];
+  float* sd = tsm;                      // [kPts16][CP]
+  float* sx = tsm + kPts16 * CP;        // [kPts16][kt][CP]
+  const int e = threadIdx.x;
+  const int tau = e / 16, cq = e % 4, iq = (e / 4) % 4;
+  float acc[4][4] = {};
+  float bsum = 0.0f;
+  const int64_t npts = (int64_t)B * K * hw;
+  for (int64_t c0 = (int64_t)blockIdx.x * kPts16; c0 < npts; c0 += (int64_t)gridDim.x * kPts16) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < kPts16 * CP; i += blockDim.x) {
+      const int pt = i / CP, co = i % CP;
+      const int64_t idx = c0 + pt;
+      sd[i] = (idx < npts && co < C) ? dz[idx * C + co] : 0.0f;
+    }
+    for (int i = threadIdx.x; i < kPts16 * kt * CP; i += blockDim.x) {
+      const int pt = i / (kt * CP), r = i % (kt * CP), tt = r / CP, ci = r % CP;
+      const int64_t idx = c0 + pt;
+      float v = 0.0f;
+      if (idx < npts && ci < C) {
+        const int64_t p = idx % hw;
+        const int k = (int)((idx / hw) % K), bc = (int)(idx / (hw * K));
+        const int kk = k - (kt - 1) + tt;
+        if (kk >= 0) v = in[(((int64_t)bc * K + kk) * hw + p) * C + ci];
+      }
+      sx[i] = v;
+    }
+    __syncthreads();
+    if (e < 16 * kt) {
+#pragma unroll 4
+      for (int pt = 0; pt < kPts16; ++pt) {
+        const float4 d = *reinterpret_cast<const float4*>(sd + pt * CP + 4 * cq);
+        const float4 x = *reinterpret_cast<const float4*>(sx + (pt * kt + tau) * CP + 4 * iq);
+        const float dv[4] = {d.x, d.y, d.z, d.w}, xv[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[a][c] = fmaf(dv[a], xv[c], acc[a][c]);
+      }
+    } else if (e < 16 * kt + CP) {
+      const int co = e - 16 * kt;
+      for (int pt = 0; pt < kPts16; ++pt) bsum += sd[pt * CP + co];
+    }
+  }
+  if (e < 16 * kt) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int co = 4 * cq + a, ci = 4 * iq + c;
+        if (co < C && ci < C) atomicAdd(gw + (co * C + ci) * kt + tau, acc[a][c]);
+      }
+  } else if (e < 16 * kt + C) {
+    atomicAdd(gb + (e - 16 * kt), bsum);
   }
 }
 
@@ -314,15 +454,16 @@ int tforward(const float* logl, const et_train_shape* sh, const et_evsnet_weight
   const unsigned grid = (unsigned)((n + 255) / 256);
   const float* wp = net->w + twofs(L, C, kt);
   const float* bp = net->b + (int64_t)L * C;
-  tconv_fwd<true><<<grid, 256, 0, st>>>(nullptr, logl, sh->B, sh->K, hw, 1, C, kt, net->w, net->b,
-                                        nullptr, ws.act[0], wp, bp, L == 1 ? ws.I : nullptr);
+  tconv_fwd<<<grid, 256, 0, st>>>(logl, sh->B, sh->K, hw, C, kt, net->w, net->b, ws.act[0], wp, bp,
+                                  L == 1 ? ws.I : nullptr);
   ET_CHECK_LAUNCH();
   for (int l = 1; l < L; ++l) {
     // residual form: even layers close a block and add its input
     const float* res = (net->kind == ET_NET_RESIDUAL && l % 2 == 0) ? ws.act[l - 2] : nullptr;
-    tconv_fwd<false><<<grid, 256, 0, st>>>(ws.act[l - 1], nullptr, sh->B, sh->K, hw, C, C, kt,
-                                           net->w + twofs(l, C, kt), net->b + (int64_t)l * C, res,
-                                           ws.act[l], wp, bp, l == L - 1 ? ws.I : nullptr);
+    auto kern = C == CP ? tconv16_fwd<true> : tconv16_fwd<false>;
+    kern<<<grid, 256, 0, st>>>(ws.act[l - 1], sh->B, sh->K, hw, C, kt, net->w + twofs(l, C, kt),
+                               net->b + (int64_t)l * C, res, ws.act[l], wp, bp,
+                               l == L - 1 ? ws.I : nullptr);
     ET_CHECK_LAUNCH();
   }
   return ET_OK;
@@ -382,12 +523,20 @@ int et_train_temporal_backward(const float* logl, const et_train_shape* sh,
   tproj_bwd<<<nsm * 4, 256, 0, st>>>(ws.dI, ws.act[L - 1], n, C, net->w + twofs(L, C, kt), dz,
                                      grad_w + twofs(L, C, kt), grad_b + (int64_t)L * C);
   ET_CHECK_LAUNCH();
+  const int wthr = twgrad_threads(kt);
+  const size_t wsmem = sizeof(float) * kPts16 * CP * (1 + kt);
+  auto wkern = C == CP ? tconv16_bwd_weight<true> : tconv16_bwd_weight<false>;
+  int wblocks = 0;   // resident weight-gradient blocks per SM: one wave of persistent blocks
+  ET_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&wblocks, wkern, wthr, wsmem));
+  const unsigned wgrid16 = (unsigned)std::max<int64_t>(
+      1, std::min<int64_t>((int64_t)nsm * std::max(wblocks, 1), (n + kPts16 - 1) / kPts16));
+  auto dkern = C == CP ? tconv16_bwd_data<true> : tconv16_bwd_data<false>;
   auto wgrad = [&](const float* d, int l) {
     if (l == 0)
-      tconv_bwd_weight<true><<<wgrid, 256, 0, st>>>(d, nullptr, logl, B, K, hw, 1, C, kt, grad_w, grad_b);
+      tconv_bwd_weight<<<wgrid, 256, 0, st>>>(d, logl, B, K, hw, C, kt, grad_w, grad_b);
     else
-      tconv_bwd_weight<false><<<wgrid, 256, 0, st>>>(d, ws.act[l - 1], nullptr, B, K, hw, C, C, kt,
-                                                     grad_w + twofs(l, C, kt), grad_b + (int64_t)l * C);
+      wkern<<<wgrid16, wthr, wsmem, st>>>(d, ws.act[l - 1], B, K, hw, C, kt, grad_w + twofs(l, C, kt),
+                                          grad_b + (int64_t)l * C);
   };
   if (net->kind == ET_NET_STACK) {
     int cur = 0;
@@ -395,8 +544,8 @@ int et_train_temporal_backward(const float* logl, const et_train_shape* sh,
       wgrad(ws.g[cur], l);
       ET_CHECK_LAUNCH();
       if (l > 0) {
-        tconv_bwd_data<<<grid, 256, 0, st>>>(ws.g[cur], B, K, hw, C, C, kt, net->w + twofs(l, C, kt),
-                                             nullptr, ws.act[l - 1], ws.g[cur ^ 1]);
+        dkern<<<grid, 256, 0, st>>>(ws.g[cur], B, K, hw, C, kt, net->w + twofs(l, C, kt), nullptr,
+                                    ws.act[l - 1], ws.g[cur ^ 1]);
         ET_CHECK_LAUNCH();
         cur ^= 1;
       }
@@ -411,14 +560,14 @@ int et_train_temporal_backward(const float* logl, const et_train_shape* sh,
     wgrad(ws.g[cz], lc);
     ET_CHECK_LAUNCH();
     // dy = conv_lc^T(dz) masked by a > 0
-    tconv_bwd_data<<<grid, 256, 0, st>>>(ws.g[cz], B, K, hw, C, C, kt, net->w + twofs(lc, C, kt),
-                                         nullptr, ws.act[la], ws.g[cy]);
+    dkern<<<grid, 256, 0, st>>>(ws.g[cz], B, K, hw, C, kt, net->w + twofs(lc, C, kt), nullptr,
+                                ws.act[la], ws.g[cy]);
     ET_CHECK_LAUNCH();
     wgrad(ws.g[cy], la);
     ET_CHECK_LAUNCH();
     // dz_prev = (dz + conv_la^T(dy)) masked by h_{i-1} > 0
-    tconv_bwd_data<<<grid, 256, 0, st>>>(ws.g[cy], B, K, hw, C, C, kt, net->w + twofs(la, C, kt),
-                                         ws.g[cz], ws.act[la - 1], ws.g[cn]);
+    dkern<<<grid, 256, 0, st>>>(ws.g[cy], B, K, hw, C, kt, net->w + twofs(la, C, kt), ws.g[cz],
+                                ws.act[la - 1], ws.g[cn]);
     ET_CHECK_LAUNCH();
     cz = cn;
   }
