@@ -251,9 +251,11 @@ __device__ __forceinline__ void load_ch(const float* __restrict__ src, int C, fl
   }
 }
 
-// acc[o] += sum_i w[i][o] x[i] for one tap's 16 x 16 block of shared weights
-__device__ __forceinline__ void fma_block(const float* __restrict__ w, const float (&x)[CP], int C,
-                                          float (&acc)[CP]) {
+// acc0[o] += sum_i w[i][o] x0[i] and acc1[o] += sum_i w[i][o] x1[i] for one tap's
+// 16 x 16 block of shared weights: two steps per weight load
+__device__ __forceinline__ void fma_block2(const float* __restrict__ w, const float (&x0)[CP],
+                                           const float (&x1)[CP], int C, float (&acc0)[CP],
+                                           float (&acc1)[CP]) {
 #pragma unroll
   for (int i = 0; i < CP; ++i) {
     if (i >= C) break;
@@ -261,18 +263,36 @@ __device__ __forceinline__ void fma_block(const float* __restrict__ w, const flo
 #pragma unroll
     for (int j = 0; j < CP / 4; ++j) {
       const float4 v = w4[j];
-      acc[4 * j] = fmaf(v.x, x[i], acc[4 * j]);
-      acc[4 * j + 1] = fmaf(v.y, x[i], acc[4 * j + 1]);
-      acc[4 * j + 2] = fmaf(v.z, x[i], acc[4 * j + 2]);
-      acc[4 * j + 3] = fmaf(v.w, x[i], acc[4 * j + 3]);
+      acc0[4 * j] = fmaf(v.x, x0[i], acc0[4 * j]);
+      acc0[4 * j + 1] = fmaf(v.y, x0[i], acc0[4 * j + 1]);
+      acc0[4 * j + 2] = fmaf(v.z, x0[i], acc0[4 * j + 2]);
+      acc0[4 * j + 3] = fmaf(v.w, x0[i], acc0[4 * j + 3]);
+      acc1[4 * j] = fmaf(v.x, x1[i], acc1[4 * j]);
+      acc1[4 * j + 1] = fmaf(v.y, x1[i], acc1[4 * j + 1]);
+      acc1[4 * j + 2] = fmaf(v.z, x1[i], acc1[4 * j + 2]);
+      acc1[4 * j + 3] = fmaf(v.w, x1[i], acc1[4 * j + 3]);
     }
   }
 }
 
-// forward of a C -> C layer: out = ReLU(b + conv(in) [+ res]), the last layer
-// also I = bp + wp . out; one thread per (clip, step, pixel)
+// a pixel-step's channels, zero outside the clip's steps [0, K)
 template <bool kC16>
-__global__ void __launch_bounds__(256, 4)
+__device__ __forceinline__ void load_step(const float* __restrict__ base, int k, int K, int64_t step,
+                                          int C, float (&x)[CP]) {
+  if (k < 0 || k >= K) {
+#pragma unroll
+    for (int c = 0; c < CP; ++c) x[c] = 0.0f;
+  } else {
+    load_ch<kC16>(base + k * step, C, x);
+  }
+}
+
+// forward of a C -> C layer: out = ReLU(b + conv(in) [+ res]), the last layer
+// also I = bp + wp . out.  One thread per (clip, pair of steps 2j and 2j + 1,
+// pixel): each tap's weights serve both steps, the input of step k - kt + 2 + tau
+// serving the second step at tap tau and the first at tau + 1.
+template <bool kC16>
+__global__ void __launch_bounds__(256, 3)
 tconv16_fwd(const float* __restrict__ in, int B, int K, int64_t hw, int C, int kt,
             const float* __restrict__ w, const float* __restrict__ b, const float* __restrict__ res,
             float* __restrict__ out, const float* __restrict__ wp, const float* __restrict__ bp,
@@ -283,45 +303,55 @@ tconv16_fwd(const float* __restrict__ in, int B, int K, int64_t hw, int C, int k
     sw[i] = (co < C && ci < C) ? w[(co * C + ci) * kt + tau] : 0.0f;
   }
   __syncthreads();
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)B * K * hw) return;
-  const int64_t p = idx % hw;
-  const int k = (int)((idx / hw) % K), bc = (int)(idx / (hw * K));
-  float acc[CP];
+  const int KP = (K + 1) / 2;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)B * KP * hw) return;
+  const int64_t p = t % hw;
+  const int k = 2 * (int)((t / hw) % KP), bc = (int)(t / (hw * KP));
+  const int64_t step = hw * C;
+  const float* base = in + ((int64_t)bc * K * hw + p) * C;
+  float acc0[CP], acc1[CP];
 #pragma unroll
-  for (int co = 0; co < CP; ++co) acc[co] = co < C ? b[co] : 0.0f;
+  for (int co = 0; co < CP; ++co) acc0[co] = acc1[co] = co < C ? b[co] : 0.0f;
+  float xa[CP];
+  load_step<kC16>(base, k - (kt - 1), K, step, C, xa);
   for (int tau = 0; tau < kt; ++tau) {
-    const int kk = k - (kt - 1) + tau;
-    if (kk < 0) continue;
-    float x[CP];
-    load_ch<kC16>(in + (((int64_t)bc * K + kk) * hw + p) * C, C, x);
-    fma_block(sw + tau * CP * CP, x, C, acc);
-  }
-  float Iv = bp ? bp[0] : 0.0f;
+    float xb[CP];
+    load_step<kC16>(base, k - (kt - 1) + tau + 1, K, step, C, xb);
+    fma_block2(sw + tau * CP * CP, xa, xb, C, acc0, acc1);
 #pragma unroll
-  for (int co = 0; co < CP; ++co) {
-    if (co >= C) break;
-    const float z = res ? acc[co] + res[idx * C + co] : acc[co];
-    acc[co] = fmaxf(z, 0.0f);
-    if (I) Iv += wp[co] * acc[co];
+    for (int c = 0; c < CP; ++c) xa[c] = xb[c];
   }
-  if (kC16) {
+  auto finish = [&](float (&acc)[CP], int h) {
+    const int64_t idx = ((int64_t)bc * K + k + h) * hw + p;
+    float Iv = bp ? bp[0] : 0.0f;
 #pragma unroll
-    for (int j = 0; j < CP / 4; ++j)
-      reinterpret_cast<float4*>(out + idx * C)[j] =
-          make_float4(acc[4 * j], acc[4 * j + 1], acc[4 * j + 2], acc[4 * j + 3]);
-  } else {
+    for (int co = 0; co < CP; ++co) {
+      if (co >= C) break;
+      const float z = res ? acc[co] + res[idx * C + co] : acc[co];
+      acc[co] = fmaxf(z, 0.0f);
+      if (I) Iv += wp[co] * acc[co];
+    }
+    if (kC16) {
 #pragma unroll
-    for (int co = 0; co < CP; ++co)
-      if (co < C) out[idx * C + co] = acc[co];
-  }
-  if (I) I[idx] = Iv;
+      for (int j = 0; j < CP / 4; ++j)
+        reinterpret_cast<float4*>(out + idx * C)[j] =
+            make_float4(acc[4 * j], acc[4 * j + 1], acc[4 * j + 2], acc[4 * j + 3]);
+    } else {
+#pragma unroll
+      for (int co = 0; co < CP; ++co)
+        if (co < C) out[idx * C + co] = acc[co];
+    }
+    if (I) I[idx] = Iv;
+  };
+  finish(acc0, 0);
+  if (k + 1 < K) finish(acc1, 1);
 }
 
 // data backward: out[s][ci] = (add[s][ci] + sum_tau,co w[co][ci][tau] dz[s + kt - 1 - tau][co])
-// 1(mask[s][ci] > 0); weights staged [tau][co][ci]
+// 1(mask[s][ci] > 0); weights staged [tau][co][ci]; two steps per thread as above
 template <bool kC16>
-__global__ void __launch_bounds__(256, 4)
+__global__ void __launch_bounds__(256, 3)
 tconv16_bwd_data(const float* __restrict__ dz, int B, int K, int64_t hw, int C, int kt,
                  const float* __restrict__ w, const float* __restrict__ add,
                  const float* __restrict__ mask, float* __restrict__ out) {
@@ -331,27 +361,37 @@ tconv16_bwd_data(const float* __restrict__ dz, int B, int K, int64_t hw, int C, 
     sw[i] = (co < C && ci < C) ? w[(co * C + ci) * kt + tau] : 0.0f;
   }
   __syncthreads();
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)B * K * hw) return;
-  const int64_t p = idx % hw;
-  const int s = (int)((idx / hw) % K), bc = (int)(idx / (hw * K));
-  float acc[CP];
+  const int KP = (K + 1) / 2;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)B * KP * hw) return;
+  const int64_t p = t % hw;
+  const int s = 2 * (int)((t / hw) % KP), bc = (int)(t / (hw * KP));
+  const int64_t step = hw * C;
+  const float* base = dz + ((int64_t)bc * K * hw + p) * C;
+  float acc0[CP], acc1[CP];
 #pragma unroll
-  for (int ci = 0; ci < CP; ++ci) acc[ci] = 0.0f;
+  for (int ci = 0; ci < CP; ++ci) acc0[ci] = acc1[ci] = 0.0f;
+  float gb[CP];   // dz[s + kt - tau] for the second step
+  load_step<kC16>(base, s + kt, K, step, C, gb);
   for (int tau = 0; tau < kt; ++tau) {
-    const int k = s + kt - 1 - tau;
-    if (k >= K) continue;
-    float g[CP];
-    load_ch<kC16>(dz + (((int64_t)bc * K + k) * hw + p) * C, C, g);
-    fma_block(sw + tau * CP * CP, g, C, acc);
-  }
+    float ga[CP];
+    load_step<kC16>(base, s + kt - 1 - tau, K, step, C, ga);
+    fma_block2(sw + tau * CP * CP, ga, gb, C, acc0, acc1);
 #pragma unroll
-  for (int ci = 0; ci < CP; ++ci) {
-    if (ci >= C) break;
-    const int64_t o = idx * C + ci;
-    const float v = add ? add[o] + acc[ci] : acc[ci];
-    out[o] = mask[o] > 0.0f ? v : 0.0f;
+    for (int c = 0; c < CP; ++c) gb[c] = ga[c];
   }
+  auto finish = [&](const float (&acc)[CP], int h) {
+    const int64_t idx = ((int64_t)bc * K + s + h) * hw + p;
+#pragma unroll
+    for (int ci = 0; ci < CP; ++ci) {
+      if (ci >= C) break;
+      const int64_t o = idx * C + ci;
+      const float v = add ? add[o] + acc[ci] : acc[ci];
+      out[o] = mask[o] > 0.0f ? v : 0.0f;
+    }
+  };
+  finish(acc0, 0);
+  if (s + 1 < K) finish(acc1, 1);
 }
 
 // weight backward of a C -> C layer: grad w[co][ci][tau] += sum dz[k][co] in[k - kt + 1 + tau][ci],
@@ -369,29 +409,53 @@ tconv16_bwd_weight(const float* __restrict__ dz, const float* __restrict__ in, i
   extern __shared__ __align__(16) float tsm[];
   float* sd = tsm;                      // [kPts16][CP]
   float* sx = tsm + kPts16 * CP;        // [kPts16][kt][CP]
+  __shared__ int64_t s_row0[kPts16];    // offset of the point's pixel at step 0 of its clip
+  __shared__ int s_k[kPts16];           // the point's step, -1 past the end
   const int e = threadIdx.x;
   const int tau = e / 16, cq = e % 4, iq = (e / 4) % 4;
   float acc[4][4] = {};
   float bsum = 0.0f;
-  const int64_t npts = (int64_t)B * K * hw;
+  const int64_t npts = (int64_t)B * K * hw, step = hw * C;
   for (int64_t c0 = (int64_t)blockIdx.x * kPts16; c0 < npts; c0 += (int64_t)gridDim.x * kPts16) {
     __syncthreads();
-    for (int i = threadIdx.x; i < kPts16 * CP; i += blockDim.x) {
-      const int pt = i / CP, co = i % CP;
+    for (int pt = threadIdx.x; pt < kPts16; pt += blockDim.x) {
       const int64_t idx = c0 + pt;
-      sd[i] = (idx < npts && co < C) ? dz[idx * C + co] : 0.0f;
-    }
-    for (int i = threadIdx.x; i < kPts16 * kt * CP; i += blockDim.x) {
-      const int pt = i / (kt * CP), r = i % (kt * CP), tt = r / CP, ci = r % CP;
-      const int64_t idx = c0 + pt;
-      float v = 0.0f;
-      if (idx < npts && ci < C) {
+      if (idx < npts) {
         const int64_t p = idx % hw;
         const int k = (int)((idx / hw) % K), bc = (int)(idx / (hw * K));
-        const int kk = k - (kt - 1) + tt;
-        if (kk >= 0) v = in[(((int64_t)bc * K + kk) * hw + p) * C + ci];
+        s_row0[pt] = ((int64_t)bc * K * hw + p) * C;
+        s_k[pt] = k;
+      } else {
+        s_row0[pt] = 0;
+        s_k[pt] = -1;
       }
-      sx[i] = v;
+    }
+    __syncthreads();
+    if (kC16) {
+      for (int i = threadIdx.x; i < kPts16 * 4; i += blockDim.x) {
+        const int pt = i >> 2, j = i & 3;
+        float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (s_k[pt] >= 0) v = __ldg(reinterpret_cast<const float4*>(dz + (c0 + pt) * CP) + j);
+        reinterpret_cast<float4*>(sd)[i] = v;
+      }
+      for (int i = threadIdx.x; i < kPts16 * kt * 4; i += blockDim.x) {
+        const int pt = i / (kt * 4), r = i % (kt * 4), tt = r >> 2, j = r & 3;
+        const int kk = s_k[pt] - (kt - 1) + tt;
+        float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (s_k[pt] >= 0 && kk >= 0)
+          v = __ldg(reinterpret_cast<const float4*>(in + s_row0[pt] + kk * step) + j);
+        reinterpret_cast<float4*>(sx)[i] = v;
+      }
+    } else {
+      for (int i = threadIdx.x; i < kPts16 * CP; i += blockDim.x) {
+        const int pt = i / CP, co = i % CP;
+        sd[i] = (s_k[pt] >= 0 && co < C) ? dz[(c0 + pt) * C + co] : 0.0f;
+      }
+      for (int i = threadIdx.x; i < kPts16 * kt * CP; i += blockDim.x) {
+        const int pt = i / (kt * CP), r = i % (kt * CP), tt = r / CP, ci = r % CP;
+        const int kk = s_k[pt] - (kt - 1) + tt;
+        sx[i] = (s_k[pt] >= 0 && kk >= 0 && ci < C) ? in[s_row0[pt] + kk * step + ci] : 0.0f;
+      }
     }
     __syncthreads();
     if (e < 16 * kt) {
@@ -452,6 +516,7 @@ int tforward(const float* logl, const et_train_shape* sh, const et_evsnet_weight
   const int C = net->C, L = net->n_layers, kt = net->kt;
   const int64_t hw = (int64_t)sh->H * sh->W, n = (int64_t)sh->B * sh->K * hw;
   const unsigned grid = (unsigned)((n + 255) / 256);
+  const unsigned grid2 = (unsigned)(((int64_t)sh->B * ((sh->K + 1) / 2) * hw + 255) / 256);   // step pairs
   const float* wp = net->w + twofs(L, C, kt);
   const float* bp = net->b + (int64_t)L * C;
   tconv_fwd<<<grid, 256, 0, st>>>(logl, sh->B, sh->K, hw, C, kt, net->w, net->b, ws.act[0], wp, bp,
@@ -461,7 +526,7 @@ int tforward(const float* logl, const et_train_shape* sh, const et_evsnet_weight
     // residual form: even layers close a block and add its input
     const float* res = (net->kind == ET_NET_RESIDUAL && l % 2 == 0) ? ws.act[l - 2] : nullptr;
     auto kern = C == CP ? tconv16_fwd<true> : tconv16_fwd<false>;
-    kern<<<grid, 256, 0, st>>>(ws.act[l - 1], sh->B, sh->K, hw, C, kt, net->w + twofs(l, C, kt),
+    kern<<<grid2, 256, 0, st>>>(ws.act[l - 1], sh->B, sh->K, hw, C, kt, net->w + twofs(l, C, kt),
                                net->b + (int64_t)l * C, res, ws.act[l], wp, bp,
                                l == L - 1 ? ws.I : nullptr);
     ET_CHECK_LAUNCH();
@@ -517,7 +582,7 @@ int et_train_temporal_backward(const float* logl, const et_train_shape* sh,
       ws.I, B, K, hw, sh->ckpt_every, n_ckpt, net->beta, net->vth, net->reset, alpha, V_ckpt, dS_on,
       dS_off, ws.dI);
   ET_CHECK_LAUNCH();
-  const unsigned grid = (unsigned)((n + 255) / 256);
+  const unsigned grid2 = (unsigned)((npx * ((K + 1) / 2) + 255) / 256);   // step pairs
   const unsigned wgrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(nsm * 8, (n + kPts - 1) / kPts));
   float* dz = ws.g[0];
   tproj_bwd<<<nsm * 4, 256, 0, st>>>(ws.dI, ws.act[L - 1], n, C, net->w + twofs(L, C, kt), dz,
@@ -544,7 +609,7 @@ int et_train_temporal_backward(const float* logl, const et_train_shape* sh,
       wgrad(ws.g[cur], l);
       ET_CHECK_LAUNCH();
       if (l > 0) {
-        dkern<<<grid, 256, 0, st>>>(ws.g[cur], B, K, hw, C, kt, net->w + twofs(l, C, kt), nullptr,
+        dkern<<<grid2, 256, 0, st>>>(ws.g[cur], B, K, hw, C, kt, net->w + twofs(l, C, kt), nullptr,
                                     ws.act[l - 1], ws.g[cur ^ 1]);
         ET_CHECK_LAUNCH();
         cur ^= 1;
@@ -560,13 +625,13 @@ int et_train_temporal_backward(const float* logl, const et_train_shape* sh,
     wgrad(ws.g[cz], lc);
     ET_CHECK_LAUNCH();
     // dy = conv_lc^T(dz) masked by a > 0
-    dkern<<<grid, 256, 0, st>>>(ws.g[cz], B, K, hw, C, kt, net->w + twofs(lc, C, kt), nullptr,
+    dkern<<<grid2, 256, 0, st>>>(ws.g[cz], B, K, hw, C, kt, net->w + twofs(lc, C, kt), nullptr,
                                 ws.act[la], ws.g[cy]);
     ET_CHECK_LAUNCH();
     wgrad(ws.g[cy], la);
     ET_CHECK_LAUNCH();
     // dz_prev = (dz + conv_la^T(dy)) masked by h_{i-1} > 0
-    dkern<<<grid, 256, 0, st>>>(ws.g[cy], B, K, hw, C, kt, net->w + twofs(la, C, kt), ws.g[cz],
+    dkern<<<grid2, 256, 0, st>>>(ws.g[cy], B, K, hw, C, kt, net->w + twofs(la, C, kt), ws.g[cz],
                                 ws.act[la - 1], ws.g[cn]);
     ET_CHECK_LAUNCH();
     cz = cn;
