@@ -26,7 +26,6 @@ namespace {
 
 constexpr int TW = 32, TH = 16;
 constexpr int CP = 16;            // channels as stored (C <= 16, zero padded)
-constexpr int kThreads = 256, kWarps = kThreads / 32;
 
 struct SParams {
   int L;
@@ -42,6 +41,7 @@ __device__ __forceinline__ float4 relu4(float a, float b, float c, float d) {
   return make_float4(fmaxf(a, 0.0f), fmaxf(b, 0.0f), fmaxf(c, 0.0f), fmaxf(d, 0.0f));
 }
 
+template <int kThreads>
 __global__ void __launch_bounds__(kThreads)
 evsnet_f32s_kernel(SParams P, int C, const float* __restrict__ logl, const float* __restrict__ wg,
                    const float* __restrict__ bg, float* __restrict__ Vg,
@@ -50,6 +50,7 @@ evsnet_f32s_kernel(SParams P, int C, const float* __restrict__ logl, const float
                    int8_t* __restrict__ spikes) {
   extern __shared__ __align__(16) float sm[];
   const int L = P.L, Wp = P.Wp, Hp = P.Hp, tid = threadIdx.x;
+  constexpr int kWarps = kThreads / 32;
   const int warp = tid >> 5, lane = tid & 31, pg = lane >> 2, cg = lane & 3;
   float* const act0 = sm;                         // [Hp Wp][CP], permuted groups
   float* const act1 = sm + P.off_act1;
@@ -164,7 +165,7 @@ evsnet_f32s_kernel(SParams P, int C, const float* __restrict__ logl, const float
         for (int k = 0; k < 4; ++k)
 #pragma unroll
           for (int c = 0; c < 4; ++c) acc[k][c] = sb[l * CP + 4 * cg + c];
-#pragma unroll 1
+#pragma unroll 3
         for (int t = 0; t < 9; ++t) {
           const int toff = (t / 3 - 1) * Wp + (t % 3 - 1);
           const float* wt = wlay + t * CP * CP;
@@ -282,12 +283,19 @@ int et_evsnet_forward_f32s(const float* logl, int32_t F, const et_evsnet_weights
   ET_CHECK_CUDA(cudaGetDevice(&dev));
   ET_CHECK_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   if (smem > (size_t)max_smem) return ET_ERR_UNIMPLEMENTED;
-  ET_CHECK_CUDA(cudaFuncSetAttribute(evsnet_f32s_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem));
+  int sm_smem = 0;
+  ET_CHECK_CUDA(cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+  // one CTA per SM (deep networks: the activation buffers take most of the
+  // shared memory) gets 16 warps to hide the shared-memory latency; two or
+  // more per SM keep 8 warps each (a finer split of the layer regions)
   const int tiles = ((P.W + TW - 1) / TW) * ((P.H + TH - 1) / TH);
-  evsnet_f32s_kernel<<<tiles, kThreads, smem, stream>>>(
-      P, net->C, logl, net->w, net->b, st->V, st->last_l, events, cap,
-      reinterpret_cast<unsigned long long*>(n_events), I_out, spikes);
-  ET_CHECK_LAUNCH();
-  return ET_OK;
+  auto run = [&](auto kern, int threads) -> int {
+    ET_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<tiles, threads, smem, stream>>>(P, net->C, logl, net->w, net->b, st->V, st->last_l, events, cap,
+                                           reinterpret_cast<unsigned long long*>(n_events), I_out, spikes);
+    ET_CHECK_LAUNCH();
+    return ET_OK;
+  };
+  if (2 * (smem + 1024) > (size_t)sm_smem) return run(evsnet_f32s_kernel<512>, 512);
+  return run(evsnet_f32s_kernel<256>, 256);
 }

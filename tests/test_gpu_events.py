@@ -310,3 +310,22 @@ def test_evsnet_bf16_full_size(api, orc):
         o, s = oI[:, iy:iy + 64, ix:ix + 64], S[:, iy:iy + 64, ix:ix + 64]
         g = I16[:, y0:y0 + 64, x0:x0 + 64]
         assert (np.abs(g - o) / s).max() <= 4 * U_BF16
+
+
+def test_evsnet_f32_full_size(api, orc):
+    """1280 x 720, 6 frames, the benchmark's network shape in FP32: the current
+    of 64 x 64 crops at the corners, the middle and the ragged last tile row /
+    column within 1e-5 (1 + |I|) of the oracle's."""
+    from paper_2508_18071_gb300 import _lib
+    d = inputs.random_evsnet(0, 4, 16, 1, 3, seed=12, vth=0.1, beta=0.9)
+    lf = inputs.random_logl_clip(9, 6, 720, 1280, step_std=0.4)
+    _, I32, _, _ = _run(api, d, lf, _lib.ET_F32)
+    for (y0, x0) in [(0, 0), (300, 600), (656, 1216), (700, 40), (20, 1250)]:
+        ya, xa = max(0, y0 - 4), max(0, x0 - 4)
+        yb, xb = min(720, y0 + 68), min(1280, x0 + 68)
+        oI, _ = _oracle_I_and_scale(orc, d, lf[:, ya:yb, xa:xb])
+        iy, ix = y0 - ya, x0 - xa
+        o = oI[:, iy:iy + 64, ix:ix + 64]
+        g = I32[:, y0:y0 + 64, x0:x0 + 64]
+        assert g.shape == o.shape
+        assert (np.abs(g - o) <= 1e-5 * (1 + np.abs(o))).all()
