@@ -627,6 +627,16 @@ def main():
                           logl=lm, want_rgb=False)
         st2 = api.EvsStateDev(net, H_, W_)
         m_ev = api.evsnet_forward(lm, net, st2, t0=first + 10000)[0].host()
+        # the same frames with the EvSNet state carried in from the WARM frames of
+        # the path before them (a video in progress rather than a fresh start)
+        WARM = 64
+        lw = torch.empty((WARM, H_, W_), dtype=torch.float32, device=dev)
+        api.render_frames(g, inputs.city_path(WARM, first=first + 10000 - WARM), W_, H_, args.spp,
+                          DEPTH, SEED, first_frame=first + 10000 - WARM, logl=lw, want_rgb=False)
+        st3 = api.EvsStateDev(net, H_, W_)
+        api.evsnet_forward(lw, net, st3, t0=first + 10000 - WARM)
+        mw_ev = api.evsnet_forward(lm, net, st3, t0=first + 10000)[0].host()
+        del lw
         ref2 = torch.zeros(npix, dtype=torch.float64, device=dev)
         t_ev = api.threshold_events(lm, C_THR, ref2, False, t0=first + 10000).host()
         line["baseline_256spp_threshold"] = {
@@ -634,6 +644,8 @@ def main():
             "speedup_of_method": value / base_value}
         line["event_f1_vs_baseline"] = {
             "delta_frames": 1, "frames": nb - 1, "method": api.event_f1(m_ev, ref_ev, 1),
+            "method_state_warmed": api.event_f1(mw_ev, ref_ev, 1), "warm_frames": WARM,
+            "n_method_state_warmed": len(mw_ev),
             "threshold_on_low_spp": api.event_f1(t_ev, ref_ev, 1),
             "ceiling_second_256spp_render": api.event_f1(ref2_ev, ref_ev, 1),
             "n_ref": len(ref_ev), "n_method": len(m_ev), "n_threshold_low_spp": len(t_ev),

@@ -25,6 +25,7 @@ namespace {
 
 constexpr unsigned FULL = 0xFFFFFFFFu;
 constexpr int kLeafBatch = 24;       // lanes waiting at leaves that end a node phase
+constexpr int kNodeSteps = 3;        // node visits per lane between two warp votes
 constexpr int64_t kPathCap = 8 << 20;
 
 enum { C_NRAY0 = 0, C_NRAY1 = 1, C_NSH = 2, C_FETCH = 3, C_FETCH_SH = 4, C_N = 8 };
@@ -142,7 +143,13 @@ __global__ void __launch_bounds__(128, ET_TRACE_MIN_BLOCKS) wf_trace(Args A, int
       if (!nodes) break;
       const unsigned leaves = __ballot_sync(FULL, idx >= 0 && tr.at_leaf());
       if (__popc(leaves) >= kLeafBatch) break;
-      if (node) tr.visit_node(A.S, ray);
+      // up to kNodeSteps steps per vote: a lane keeps descending while it is at
+      // an inner node (its own sequence of visits is unchanged)
+      if (node) {
+#pragma unroll
+        for (int r = 0; r < kNodeSteps; ++r)
+          if (tr.at_node()) tr.visit_node(A.S, ray);
+      }
     }
     // leaf phase: lanes at a leaf test its triangles together
     if (idx >= 0 && tr.at_leaf()) tr.visit_leaf(A.S, ray);
