@@ -21,6 +21,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -460,8 +461,10 @@ def main():
     if world > 1:
         dist.barrier()
     evs = []
-    out_dir = os.path.join(ROOT, "gpurun_out")
-    clk = Clocks(os.path.join(out_dir if os.path.isdir(out_dir) else "/tmp", "clocks_bench.csv"))
+    # the clock samples of the timed region (nvidia-smi CSV) go to ET_BENCH_OUT
+    out_dir = os.environ.get("ET_BENCH_OUT", "")
+    clk = Clocks(os.path.join(out_dir if os.path.isdir(out_dir) else tempfile.gettempdir(),
+                              "clocks_bench.csv"))
     torch.cuda.synchronize()
     launches0 = _lib.load().et_kernel_launches()
     wall0 = time.perf_counter()
@@ -573,7 +576,7 @@ def main():
         line["cpu_baseline"] = cpu
         flops_launch = work["flops_per_ray"] * work["rays_per_sample"] * npix * args.spp * F
         line["mrays_per_s"] = work["rays_per_sample"] * npix * args.spp * F / (statistics.mean(t_render) / 1e3) / 1e6
-        # the survey's second traversal bound: algorithmic node + triangle bytes
+        # the second traversal bound: algorithmic node + triangle bytes
         # per ray against HBM (above 1: the hierarchy is served from L1 / L2)
         bytes_launch = work["bytes_per_ray"] * work["rays_per_sample"] * npix * args.spp * F
         hbm = peaks.get("hbm_gbs") or 6800.0
