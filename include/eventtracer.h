@@ -297,7 +297,12 @@ int et_evsnet_forward(const float* logl, int32_t F, const et_evsnet_weights* net
  * the backward uses the surrogate of Eq. 4, s(x) = (alpha/2) / (1 + (pi alpha x / 2)^2),
  * on both thresholds and differentiates the reset.  The membrane starts at 0.
  * Backpropagation through time keeps V at the start of every segment of
- * ckpt_every (<= 32) steps and recomputes each segment in the backward. */
+ * ckpt_every (<= 32) steps and recomputes each segment in the backward.
+ * net->dtype: ET_F32 (everything in FP32 on the CUDA cores), or, for the
+ * spatial form only, ET_BF16: the forward and the data gradient of the
+ * C -> C convolutions (layers 1..) take BF16 operands on the tensor cores with
+ * FP32 accumulation (the workload's "BF16 convolutions, FP32 accumulation");
+ * layer 0, BiLIF, the loss, the weight gradients and the weights stay FP32. */
 typedef struct { int32_t B, K, H, W, ckpt_every; } et_train_shape;
 
 /* Bytes of the caller-allocated device workspace the two calls below need:
@@ -311,7 +316,9 @@ int et_train_workspace_bytes(const et_evsnet_weights* net, const et_train_shape*
  * optional S_on / S_off float [B][K][H][W] (both or neither), V_ckpt float
  * [B][ceil(K / ckpt_every)][H][W], optional I_out float [B][K][H][W].
  * Errors: ET_ERR_ARG, ET_ERR_UNIMPLEMENTED (a form other than the two above,
- * C > 16, dtype other than ET_F32, ckpt_every > 32), ET_ERR_CUDA. */
+ * C > 16, dtype other than ET_F32 / ET_BF16 or ET_BF16 for the temporal form,
+ * ckpt_every > 32), ET_ERR_CUDA.  With ET_BF16, a tensor-core wait that runs
+ * out of its bound (et_set_wait_budget) leaves NaN in the affected outputs. */
 int et_evsnet_train_forward(const float* logl, const et_train_shape* shape,
                             const et_evsnet_weights* net, int8_t* spikes, float* S_on,
                             float* S_off, float* V_ckpt, float* I_out, void* workspace,

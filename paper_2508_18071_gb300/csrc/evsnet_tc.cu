@@ -417,7 +417,7 @@ int launch(const float* logl, int32_t F, const et_evsnet_weights* net, et_evsnet
   while (cols < (uint32_t)(P.nb1 * CP)) cols <<= 1;
   if (cols > 512) return ET_ERR_UNIMPLEMENTED;
   P.tmem_cols = cols;
-  P.wait_iters = g_wait_budget < 0 ? kWaitIters : (uint32_t)std::min<int64_t>(g_wait_budget, 0xFFFFFFFFll);
+  P.wait_iters = et_tc_wait_iters();
   int dev = 0, max_smem = 0;
   ET_CHECK_CUDA(cudaGetDevice(&dev));
   ET_CHECK_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
@@ -434,6 +434,10 @@ int launch(const float* logl, int32_t F, const et_evsnet_weights* net, et_evsnet
 }  // namespace
 
 extern "C" void et_set_wait_budget(int64_t polls) { g_wait_budget = polls; }
+
+uint32_t et_tc_wait_iters() {
+  return g_wait_budget < 0 ? kWaitIters : (uint32_t)std::min<int64_t>(g_wait_budget, 0xFFFFFFFFll);
+}
 
 int et_evsnet_forward_tc(const float* logl, int32_t F, const et_evsnet_weights* net,
                          et_evsnet_state* st, int32_t t0, et_event* events, int64_t cap,

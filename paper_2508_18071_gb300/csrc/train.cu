@@ -2,6 +2,8 @@
 // BiLIF; the paper's temporal form is in train_temporal.cu and is dispatched
 // from the entry points below) on the GPU: forward with membrane checkpoints, the paper's loss
 // (Eq. 7-11) with its gradient, surrogate-gradient BPTT (Eq. 4), and Adam.
+// FP32 throughout, or with BF16 weights the C -> C convolutions' forward and
+// data gradient on the tensor cores (train_tc.cu).
 //
 // Layout: B clips of K steps of H x W pixels.  Time is processed in segments of
 // `ckpt_every` steps.  The forward keeps only the membrane potential V at the
@@ -601,10 +603,11 @@ bool layout(const et_evsnet_weights* net, const et_train_shape* sh, char* base, 
 int check(const et_evsnet_weights* net, const et_train_shape* sh) {
   if (!net || !sh || !net->w || !net->b) return ET_ERR_ARG;
   if (sh->B < 1 || sh->K < 1 || sh->H < 1 || sh->W < 1 || sh->ckpt_every < 1) return ET_ERR_ARG;
-  if (net->n_layers < 1 || net->n_layers > kMaxLayers || net->C < 1 || net->dtype != ET_F32)
-    return ET_ERR_UNIMPLEMENTED;
+  if (net->n_layers < 1 || net->n_layers > kMaxLayers || net->C < 1) return ET_ERR_UNIMPLEMENTED;
   const bool spatial = net->kind == ET_NET_STACK && net->ks == 3 && net->kt == 1 && net->C <= kMaxC;
   if (!spatial && !et_train_is_temporal(net)) return ET_ERR_UNIMPLEMENTED;
+  // BF16: the spatial form's C -> C convolutions on the tensor cores
+  if (net->dtype != ET_F32 && !(net->dtype == ET_BF16 && spatial)) return ET_ERR_UNIMPLEMENTED;
   if (sh->ckpt_every > kMaxSeg) return ET_ERR_UNIMPLEMENTED;
   return ET_OK;
 }
@@ -622,7 +625,12 @@ int seg_forward(const float* logl, const et_train_shape* sh, const et_evsnet_wei
     if (l == 0)
       conv_fwd<<<grid, TS * TS, 0, st>>>(logl, sh->K, k0, nseg, C, H, W, net->w, net->b, ws.act[0],
                                          wproj, bproj, last ? ws.I : nullptr);
-    else
+    else if (net->dtype == ET_BF16) {
+      const int rc = et_train_tc_conv(ws.act[l - 1], N, C, H, W, net->w + wofs(l, C),
+                                      net->b + (int64_t)l * C, ws.act[l], wproj, bproj,
+                                      last ? ws.I : nullptr, nullptr, false, st);
+      if (rc != ET_OK) return rc;
+    } else
       conv16_fwd<<<grid, TS * TS, 0, st>>>(ws.act[l - 1], C, H, W, net->w + wofs(l, C),
                                            net->b + (int64_t)l * C, ws.act[l], wproj, bproj,
                                            last ? ws.I : nullptr);
@@ -750,9 +758,15 @@ extern "C" int et_evsnet_train_backward(const float* logl, const et_train_shape*
                                                                grad_w + wofs(l, C), grad_b + (int64_t)l * C);
       ET_CHECK_LAUNCH();
       if (l > 0) {
-        conv16_bwd_data<<<grid, TS * TS, 0, st>>>(ws.dz[cur], C, H, W, net->w + wofs(l, C),
-                                                  ws.act[l - 1], ws.dz[cur ^ 1]);
-        ET_CHECK_LAUNCH();
+        if (net->dtype == ET_BF16) {
+          rc = et_train_tc_conv(ws.dz[cur], N, C, H, W, net->w + wofs(l, C), nullptr, ws.dz[cur ^ 1],
+                                nullptr, nullptr, nullptr, ws.act[l - 1], true, st);
+          if (rc != ET_OK) return rc;
+        } else {
+          conv16_bwd_data<<<grid, TS * TS, 0, st>>>(ws.dz[cur], C, H, W, net->w + wofs(l, C),
+                                                    ws.act[l - 1], ws.dz[cur ^ 1]);
+          ET_CHECK_LAUNCH();
+        }
         cur ^= 1;
       }
     }

@@ -19,3 +19,11 @@ int et_train_temporal_backward(const float* logl, const et_train_shape* sh,
                                const et_evsnet_weights* net, const float* V_ckpt,
                                const float* dS_on, const float* dS_off, float alpha,
                                float* grad_w, float* grad_b, void* workspace, cudaStream_t st);
+
+// The spatial form's C -> C 3x3 layers on the tensor cores (BF16 operands, FP32
+// accumulation; train_tc.cu), N images of C <= 16 plane-major channels:
+// forward out = ReLU(conv(in) + b), with I = bp + wp . out when I is not NULL;
+// or, with data_grad, out = conv^T(in) * 1(a_prev > 0).
+int et_train_tc_conv(const float* in, int N, int C, int H, int W, const float* w, const float* b,
+                     float* out, const float* wp, const float* bp, float* I, const float* a_prev,
+                     bool data_grad, cudaStream_t stream);

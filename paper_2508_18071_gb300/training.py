@@ -27,8 +27,10 @@ def _shape(B, K, H, W, ckpt_every):
 
 
 def _net_struct(meta: EvsNetDev, w: torch.Tensor, b: torch.Tensor):
+    # weights stay FP32; meta.dtype = ET_BF16 runs the 3x3 C -> C convolutions
+    # (forward and data gradient) on the tensor cores with BF16 operands
     return L.et_evsnet_weights(meta.kind, meta.n_layers, meta.C, meta.kt, meta.ks, meta.beta,
-                               meta.vth, meta.reset, L.ET_F32, w.data_ptr(), b.data_ptr())
+                               meta.vth, meta.reset, meta.dtype, w.data_ptr(), b.data_ptr())
 
 
 class Workspace:
@@ -159,10 +161,12 @@ class EmdCountLossFn(torch.autograd.Function):
 
 # ----------------------------------------------------------------- trainer
 class Trainer:
-    """Adam on the packed FP32 weights of a 3x3-stack EvSNet, on the GPU."""
+    """Adam on the packed FP32 weights of an EvSNet, on the GPU.  dtype ET_BF16
+    (3x3 stacks only) computes the C -> C convolutions of the forward and of the
+    data gradient with BF16 operands on the tensor cores, FP32 accumulation."""
 
-    def __init__(self, net: dict, lr=3e-3, lam=0.01, alpha=2.0, ckpt_every=16):
-        self.meta = EvsNetDev.from_dict(net)
+    def __init__(self, net: dict, lr=3e-3, lam=0.01, alpha=2.0, ckpt_every=16, dtype=L.ET_F32):
+        self.meta = EvsNetDev.from_dict(net, dtype)
         self.w = self.meta.w.clone()
         self.b = self.meta.b.clone()
         self.mw, self.vw = torch.zeros_like(self.w), torch.zeros_like(self.w)
@@ -190,7 +194,7 @@ class Trainer:
         np.savez(path, w=self.w.cpu().numpy(), b=self.b.cpu().numpy(), mw=self.mw.cpu().numpy(),
                  vw=self.vw.cpu().numpy(), mb=self.mb.cpu().numpy(), vb=self.vb.cpu().numpy(),
                  t=self.t, lr=self.lr, lam=self.lam, alpha=self.alpha, ckpt=self.ckpt,
-                 meta=np.array([m.kind, m.n_layers, m.C, m.kt, m.ks]),
+                 meta=np.array([m.kind, m.n_layers, m.C, m.kt, m.ks]), dtype=m.dtype,
                  lif=np.array([m.beta, m.vth, m.reset], np.float64))
 
     @staticmethod
@@ -201,7 +205,7 @@ class Trainer:
         net = {"kind": kind, "n_layers": n_layers, "C": C, "kt": kt, "ks": ks, "beta": beta,
                "vth": vth, "reset": reset, "w": z["w"], "b": z["b"]}
         T = Trainer(net, lr=float(z["lr"]), lam=float(z["lam"]), alpha=float(z["alpha"]),
-                    ckpt_every=int(z["ckpt"]))
+                    ckpt_every=int(z["ckpt"]), dtype=int(z["dtype"]) if "dtype" in z else L.ET_F32)
         for k in ("mw", "vw", "mb", "vb"):
             getattr(T, k).copy_(torch.as_tensor(z[k]))
         T.t = int(z["t"])
