@@ -299,10 +299,10 @@ int et_evsnet_forward(const float* logl, int32_t F, const et_evsnet_weights* net
  * Backpropagation through time keeps V at the start of every segment of
  * ckpt_every (<= 32) steps and recomputes each segment in the backward.
  * net->dtype: ET_F32 (everything in FP32 on the CUDA cores), or, for the
- * spatial form only, ET_BF16: the forward and the data gradient of the
- * C -> C convolutions (layers 1..) take BF16 operands on the tensor cores with
- * FP32 accumulation (the workload's "BF16 convolutions, FP32 accumulation");
- * layer 0, BiLIF, the loss, the weight gradients and the weights stay FP32. */
+ * spatial form only, ET_BF16: the forward, data gradient and weight gradient
+ * of the C -> C convolutions (layers 1..) take BF16 operands on the tensor
+ * cores with FP32 accumulation (the workload's "BF16 convolutions, FP32
+ * accumulation"); layer 0, BiLIF, the loss and the weights stay FP32. */
 typedef struct { int32_t B, K, H, W, ckpt_every; } et_train_shape;
 
 /* Bytes of the caller-allocated device workspace the two calls below need:

@@ -2,8 +2,8 @@
 // BiLIF; the paper's temporal form is in train_temporal.cu and is dispatched
 // from the entry points below) on the GPU: forward with membrane checkpoints, the paper's loss
 // (Eq. 7-11) with its gradient, surrogate-gradient BPTT (Eq. 4), and Adam.
-// FP32 throughout, or with BF16 weights the C -> C convolutions' forward and
-// data gradient on the tensor cores (train_tc.cu).
+// FP32 throughout, or with BF16 weights the C -> C convolutions' forward, data
+// and weight gradients on the tensor cores (train_tc.cu).
 //
 // Layout: B clips of K steps of H x W pixels.  Time is processed in segments of
 // `ckpt_every` steps.  The forward keeps only the membrane potential V at the
@@ -753,7 +753,11 @@ extern "C" int et_evsnet_train_backward(const float* logl, const et_train_shape*
       if (l == 0)
         conv_bwd_weight<<<nsm * 2, TS * TS, 0, st>>>(ws.dz[cur], logl, sh->K, k0, nseg, N, C, H, W,
                                                      grad_w + wofs(0, C), grad_b);
-      else
+      else if (net->dtype == ET_BF16) {
+        rc = et_train_tc_wgrad(ws.dz[cur], ws.act[l - 1], N, C, H, W, grad_w + wofs(l, C),
+                               grad_b + (int64_t)l * C, st);
+        if (rc != ET_OK) return rc;
+      } else
         conv16_bwd_weight<<<nsm * wblocks, kWThreads, 0, st>>>(ws.dz[cur], ws.act[l - 1], N, C, H, W,
                                                                grad_w + wofs(l, C), grad_b + (int64_t)l * C);
       ET_CHECK_LAUNCH();

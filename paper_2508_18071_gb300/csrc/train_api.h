@@ -27,3 +27,8 @@ int et_train_temporal_backward(const float* logl, const et_train_shape* sh,
 int et_train_tc_conv(const float* in, int N, int C, int H, int W, const float* w, const float* b,
                      float* out, const float* wp, const float* bp, float* I, const float* a_prev,
                      bool data_grad, cudaStream_t stream);
+// The weight and bias gradients of such a layer with BF16 operands on the
+// tensor cores: grad w[co][ci][t] += sum dz[co][p] act[ci][p + off(t)],
+// grad b[co] += sum dz[co][p] (FP32 accumulation; added to gw / gb).
+int et_train_tc_wgrad(const float* dz, const float* act, int N, int C, int H, int W, float* gw,
+                      float* gb, cudaStream_t stream);

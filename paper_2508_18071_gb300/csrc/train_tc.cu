@@ -1,8 +1,8 @@
 // BF16 tensor-core convolutions for training the spatial EvSNet (the C -> C
 // 3x3 layers of Eq. 5): the forward of a layer and the data gradient through
-// it, both as implicit GEMMs on tcgen05 with BF16 operands and FP32
-// accumulation in TMEM.  Layer 0, the weight gradients, BiLIF and the loss stay
-// in FP32 on the CUDA cores (train.cu).
+// it as implicit GEMMs, and its weight gradient as an im2col GEMM, all on
+// tcgen05 with BF16 operands and FP32 accumulation in TMEM.  Layer 0, BiLIF
+// and the loss stay in FP32 on the CUDA cores (train.cu).
 //
 // One CTA computes a 32 x 15 output tile of one image.  The input tile with a
 // one-pixel halo (34 x 17 positions) is converted to BF16 into the K-major,
@@ -24,6 +24,7 @@
 #include "tc_ptx.cuh"
 #include "train_api.h"
 #include <cuda_bf16.h>
+#include <algorithm>
 
 namespace {
 
@@ -162,6 +163,158 @@ tc_conv16(const float* __restrict__ in, int C, int H, int W, const float* __rest
   if (warp == 0) tmem_dealloc(tmem, kTmemCols);
 }
 
+// ------------------------------------------------------------ weight gradient
+// grad w[co][ci][t] = sum over images and positions p of dz[co][p] a[ci][p + off(t)]
+// as a GEMM D[(t, ci)][co] = sum_p A[(t, ci)][p] B[co][p] with BF16 operands:
+// M = 144 rows (t, ci) in two M-blocks of 128 (rows 0-127: taps 0-7; rows
+// 128-143: tap 8, the rest of that block discarded), N = 16, K = positions.
+// Persistent CTAs walk 16 x 8 position tiles; per tile the FP32 activation
+// (with halo) and dz tiles are staged in shared memory by coalesced loads, then
+// the A operand is built as their im2col (each 16-byte piece = 8 consecutive x
+// of one channel, shifted by the tap) and B from 8-position pieces of dz,
+// K-major, in 16 chunks of 8 positions: A [chunk][144 rows][16 B], B [chunk][16
+// rows][16 B].
+// The accumulators stay in TMEM across all of the CTA's tiles; one atomic per
+// entry and CTA at the end.  The bias gradient (sum of dz) is summed in FP32
+// alongside.
+constexpr int WTW = 16, WTH = 8;                    // position tile
+constexpr int kChunks = WTW * WTH / 8;              // 16 K chunks of 8 positions
+constexpr int kArows = 9 * CP;                      // 144 A rows (t, ci)
+constexpr int kAbytes = ((kChunks - 1) * kArows + 256) * 16;   // the last chunk's second M-block reads 256 rows
+constexpr int kBbytes = kChunks * CP * 16;
+constexpr uint32_t kWTmemCols = 32;                 // two M-blocks x 16 columns
+
+__global__ void __launch_bounds__(kThreads)
+tc_wgrad16(const float* __restrict__ dz, const float* __restrict__ act, int N, int C, int H, int W,
+           float* __restrict__ gw, float* __restrict__ gb, uint32_t wait_iters) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  __shared__ uint64_t mma_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ float sbias[CP];
+  __shared__ int bail;
+  unsigned char* A = sm;
+  unsigned char* Bop = sm + kAbytes;
+  float* sa = reinterpret_cast<float*>(sm + kAbytes + kBbytes);   // [CP][WTH + 2][WTW + 2]
+  float* sd = sa + CP * (WTH + 2) * (WTW + 2);                     // [CP][WTH][WTW]
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t hw = (int64_t)H * W;
+  const int tiles_x = (W + WTW - 1) / WTW, tiles_y = (H + WTH - 1) / WTH;
+  const int64_t ntiles = (int64_t)N * tiles_x * tiles_y;
+  // rows of the last chunk's second M-block beyond the 144 real ones are read
+  // by the MMA: keep them zero
+  for (int i = tid; i < (256 - kArows) * 16 / 16; i += kThreads)
+    reinterpret_cast<uint4*>(A + ((kChunks - 1) * kArows + kArows) * 16)[i] = make_uint4(0, 0, 0, 0);
+  if (tid < CP) sbias[tid] = 0.0f;
+  if (tid == 0) bail = 0;
+  if (warp == 0) tmem_alloc(&tmem_slot, kWTmemCols);
+  if (tid == 0) mbar_init(&mma_bar, 1);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  const uint32_t idesc = umma_idesc_bf16(128, CP);
+  uint32_t phase = 0;
+  bool first = true;
+  for (int64_t tile = blockIdx.x; tile < ntiles && !bail; tile += gridDim.x) {
+    const int n = (int)(tile / (tiles_x * tiles_y));
+    const int tt = (int)(tile % (tiles_x * tiles_y));
+    const int x0 = (tt % tiles_x) * WTW, y0 = (tt / tiles_x) * WTH;
+    const float* a_n = act + (int64_t)n * C * hw;
+    const float* d_n = dz + (int64_t)n * C * hw;
+    // stage the FP32 tiles with coalesced loads: activations with a one-pixel
+    // halo [ci][10][18], dz [co][8][16]
+    for (int i = tid; i < CP * (WTH + 2) * (WTW + 2); i += kThreads) {
+      const int c = i / ((WTH + 2) * (WTW + 2)), r = i % ((WTH + 2) * (WTW + 2));
+      const int y = y0 - 1 + r / (WTW + 2), x = x0 - 1 + r % (WTW + 2);
+      sa[i] = (c < C && y >= 0 && y < H && x >= 0 && x < W) ? __ldg(a_n + (int64_t)c * hw + (int64_t)y * W + x)
+                                                           : 0.0f;
+    }
+    for (int i = tid; i < CP * WTH * WTW; i += kThreads) {
+      const int c = i / (WTH * WTW), r = i % (WTH * WTW);
+      const int y = y0 + r / WTW, x = x0 + r % WTW;
+      sd[i] = (c < C && y < H && x < W) ? __ldg(d_n + (int64_t)c * hw + (int64_t)y * W + x) : 0.0f;
+    }
+    __syncthreads();
+    // A pieces: (chunk kc, row m = t * 16 + ci) = 8 consecutive x of channel ci,
+    // shifted by tap t
+    for (int i = tid; i < kChunks * kArows; i += kThreads) {
+      const int kc = i / kArows, m = i % kArows, t = m / CP, ci = m % CP;
+      const float* src = sa + (ci * (WTH + 2) + kc / 2 + t / 3) * (WTW + 2) + 8 * (kc % 2) + t % 3;
+      __align__(16) __nv_bfloat162 h[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) h[e] = __floats2bfloat162_rn(src[2 * e], src[2 * e + 1]);
+      *reinterpret_cast<uint4*>(A + (kc * kArows + m) * 16) = *reinterpret_cast<const uint4*>(h);
+    }
+    // B pieces: (chunk kc, row co); 128 threads also sum one dz row each for
+    // the bias gradient
+    for (int i = tid; i < kChunks * CP; i += kThreads) {
+      const int kc = i / CP, co = i % CP;
+      const float4* src = reinterpret_cast<const float4*>(sd + (co * WTH + kc / 2) * WTW + 8 * (kc % 2));
+      const float4 u = src[0], v = src[1];
+      __align__(16) __nv_bfloat162 h[4] = {__floats2bfloat162_rn(u.x, u.y), __floats2bfloat162_rn(u.z, u.w),
+                                           __floats2bfloat162_rn(v.x, v.y), __floats2bfloat162_rn(v.z, v.w)};
+      *reinterpret_cast<uint4*>(Bop + (kc * CP + co) * 16) = *reinterpret_cast<const uint4*>(h);
+    }
+    if (tid < CP * WTH) {
+      const float* row = sd + tid * WTW;
+      float sum = 0.0f;
+      for (int x = 0; x < WTW; ++x) sum += row[x];
+      atomicAdd(&sbias[tid / WTH], sum);
+    }
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (tid == 0) {
+      const uint32_t abase = smem_u32(A), bbase = smem_u32(Bop);
+      for (int j = 0; j < kChunks / 2; ++j) {
+        const uint64_t bd = umma_desc(bbase + (2 * j) * CP * 16, CP * 16, 128);
+        for (int mb = 0; mb < 2; ++mb) {
+          const uint64_t ad = umma_desc(abase + ((2 * j) * kArows + mb * 128) * 16, kArows * 16, 128);
+          umma_bf16(tmem + mb * CP, ad, bd, idesc, (first && j == 0) ? 0u : 1u);
+        }
+      }
+      umma_commit(&mma_bar);
+    }
+    first = false;
+    // the operands are rewritten for the next tile only after these MMAs completed
+    const bool ok = __syncthreads_and(mbar_wait(&mma_bar, phase, wait_iters) ? 1 : 0) != 0;
+    phase ^= 1u;
+    tc_fence_after();
+    if (!ok) {
+      if (tid == 0) bail = 1;
+      __syncthreads();
+    }
+  }
+  __syncthreads();
+  if (bail) {
+    // a wait ran out: the gradients of this launch are NaN; wait (bounded)
+    // for the MMAs still in flight before freeing TMEM
+    if (tid == 0) {
+      mbar_wait(&mma_bar, phase ^ 1u, kDrainIters);
+      for (int i = 0; i < C * C * 9; ++i) atomicAdd(gw + i, __int_as_float(0x7fc00000));
+    }
+  } else if (!first) {
+    // D rows (t, ci) on TMEM lanes: M-block 0 = taps 0-7 (warps 0-3), M-block 1
+    // lanes 0-15 = tap 8 (warp 4)
+    if (warp < 5) {
+      const int mb = warp == 4 ? 1 : 0;
+      float d[CP];
+      tmem_ld16(tmem + ((uint32_t)((warp & 3) * 32) << 16) + mb * CP, d);
+      const int row = mb * 128 + (warp & 3) * 32 + lane;
+      if (row < kArows) {
+        const int t = row / CP, ci = row % CP;
+        if (ci < C)
+          for (int co = 0; co < C; ++co) atomicAdd(gw + (co * C + ci) * 9 + t, d[co]);
+      }
+    }
+    if (tid < C) atomicAdd(gb + tid, sbias[tid]);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, kWTmemCols);
+}
+
 }  // namespace
 
 int et_train_tc_conv(const float* in, int N, int C, int H, int W, const float* w, const float* b,
@@ -173,6 +326,26 @@ int et_train_tc_conv(const float* in, int N, int C, int H, int W, const float* w
   dim3 grid((W + TW - 1) / TW, (H + TH - 1) / TH, N);
   tc_conv16<<<grid, kThreads, smem, stream>>>(in, C, H, W, w, b, out, wp, bp, I, a_prev, data_grad ? 1 : 0,
                                               et_tc_wait_iters());
+  ET_CHECK_LAUNCH();
+  return ET_OK;
+}
+
+int et_train_tc_wgrad(const float* dz, const float* act, int N, int C, int H, int W, float* gw,
+                      float* gb, cudaStream_t stream) {
+  if (C < 1 || C > CP) return ET_ERR_UNIMPLEMENTED;
+  const size_t smem = (size_t)kAbytes + kBbytes + sizeof(float) * CP * ((WTH + 2) * (WTW + 2) + WTH * WTW);
+  ET_CHECK_CUDA(cudaFuncSetAttribute(tc_wgrad16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int dev = 0, nsm = 0, sm_smem = 0;
+  ET_CHECK_CUDA(cudaGetDevice(&dev));
+  ET_CHECK_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  ET_CHECK_CUDA(cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+  // persistent CTAs: as many per SM as the shared memory holds (plus the static
+  // part and the per-CTA reservation), at most 8 of 256 threads; TMEM (32 of
+  // 512 columns each) is not the limit
+  const int per_sm = std::min(8, sm_smem / (int)(smem + 2048));
+  const int64_t tiles = (int64_t)N * ((W + WTW - 1) / WTW) * ((H + WTH - 1) / WTH);
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)nsm * std::max(per_sm, 1)));
+  tc_wgrad16<<<grid, kThreads, smem, stream>>>(dz, act, N, C, H, W, gw, gb, et_tc_wait_iters());
   ET_CHECK_LAUNCH();
   return ET_OK;
 }

@@ -1,9 +1,8 @@
 """BF16 tensor-core training of the 3x3 form against the FP32 path and the oracle.
 
-With net dtype ET_BF16 the C -> C convolutions of the forward and of the data
-gradient take BF16 operands (unit roundoff u = 2^-8) on the tensor cores with
-FP32 accumulation; layer 0, BiLIF, the loss and the weight gradients are the
-FP32 path's.
+With net dtype ET_BF16 the C -> C convolutions (forward, data gradient and
+weight gradient) take BF16 operands (unit roundoff u = 2^-8) on the tensor
+cores with FP32 accumulation; layer 0, BiLIF and the loss are the FP32 path's.
 
 * exact: on data whose weights and activations have few significant bits
   (+-1/2 weights, log steps in {-2..2}/4, zero biases, beta = 1) every rounding
@@ -11,9 +10,10 @@ FP32 path's.
   checkpoints equal the FP32 path's bit for bit: this pins the operand layout,
   the tap offsets, the tiles and the ragged image edges of the forward;
 * bounded: on that same forward the backward rounds each layer's gradient dz
-  to BF16 before the transposed convolution (the +-1/2 weights are exact), so
-  the weight gradients stay within 8 u (relative L2) of the FP32 path's and of
-  the oracle's; a transposed, flipped or shifted operand gives O(1) errors;
+  (and, for the weight gradient, the activations) to BF16 (the +-1/2 weights
+  are exact), so the weight gradients stay within 8 u (relative L2) of the
+  FP32 path's and of the oracle's; a transposed, flipped or shifted operand
+  gives O(1) errors;
 * training: Adam steps with BF16 convolutions lower the loss of the denoising
   task as the FP32 ones do;
 * a bounded MMA wait that runs out leaves NaN currents and a usable context."""
