@@ -26,7 +26,7 @@ import time
 import numpy as np
 import torch
 
-from . import api, inputs, training
+from . import _lib as L, api, inputs, training
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 
@@ -98,7 +98,7 @@ def make_clips(scene: api.Scene, scene_kind, seeds, n_frames, size, spp_in, spp_
 
 def train(scene_kind="city", n_clips=32, n_frames=65, size=128, spp_in=2, spp_ref=256,
           C_range=(0.2, 0.2), iters=300, batch=8, lr=3e-3, lam=0.01, C=16, n_layers=4, vth=0.2,
-          seed=0, beta=0.9, form="spatial", log=print):
+          seed=0, beta=0.9, form="spatial", dtype=L.ET_F32, log=print):
     sc_dict = inputs.city_block(seed=21) if scene_kind == "city" else inputs.random_scene(seed=11)
     scene = api.Scene(sc_dict)
     t0 = time.time()
@@ -107,7 +107,8 @@ def train(scene_kind="city", n_clips=32, n_frames=65, size=128, spp_in=2, spp_re
     torch.cuda.synchronize()
     log("data: %d clips x %d frames x %dx%d in %.1f s, %.3f target events per pixel-step"
         % (n_clips, n_frames, size, size, time.time() - t0, float(E.abs().mean())))
-    T = training.Trainer(identity_init(C, n_layers, vth, seed=seed, beta=beta, form=form), lr=lr, lam=lam)
+    T = training.Trainer(identity_init(C, n_layers, vth, seed=seed, beta=beta, form=form), lr=lr, lam=lam,
+                         dtype=dtype)
     rng = np.random.default_rng(seed)
     hist = []
     t0 = time.time()
@@ -199,11 +200,14 @@ def main():
     p.add_argument("--form", default="spatial", choices=["spatial", "temporal"],
                    help="3x3 stack of 4 layers, or the paper's temporal form (k = 7, M = 3)")
     p.add_argument("--eval-frames", type=int, default=129)
+    p.add_argument("--conv-dtype", default="f32", choices=["f32", "bf16"],
+                   help="training convolutions: FP32, or BF16 on the tensor cores (3x3 form)")
     p.add_argument("--out", default=os.path.join(HERE, "weights", "evsnet_city.npz"))
     a = p.parse_args()
     T, hist = train(a.scene, a.clips, a.frames, a.size, a.spp_in, a.spp_ref, (a.c_min, a.c_max),
                     a.iters, lr=a.lr, lam=a.lam, beta=a.beta, form=a.form,
-                    n_layers=7 if a.form == "temporal" else 4)
+                    n_layers=7 if a.form == "temporal" else 4,
+                    dtype=L.ET_BF16 if a.conv_dtype == "bf16" else L.ET_F32)
     net = T.net_dict()
     ev = evaluate(net, a.scene, n_frames=a.eval_frames)
     print("held-out:", ev)
