@@ -390,6 +390,8 @@ uint64_t et_kernel_launches(void);
  * returns; the context stays usable.  The call's previous-frame buffer and
  * `initialized` flag are still updated (the host does not see the timeout until
  * it reads the count): restore the state from a copy before retrying.
+ * The BF16 training convolutions bound their waits the same way; on expiry
+ * they write NaN into the outputs they own (activations, currents, gradients).
  * et_set_wait_budget(polls) sets the first bound for launches made afterwards in
  * this process: polls >= 0 sets it (0 gives up at once and forces the timeout
  * path, for testing the detection), polls < 0 restores the default.  (A poll
