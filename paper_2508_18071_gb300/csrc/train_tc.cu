@@ -47,7 +47,7 @@ static_assert(kLead >= Wp + 1 - kMStart, "the lead rows cover the first block's 
 __device__ __forceinline__ int tap_offset(int t) { return (t / 3 - 1) * Wp + (t % 3 - 1); }
 
 __global__ void __launch_bounds__(kThreads)
-tc_conv16(const float* __restrict__ in, int C, int H, int W, const float* __restrict__ w,
+tc_conv16(const float* __restrict__ in, int N, int C, int H, int W, const float* __restrict__ w,
           const float* __restrict__ b, float* __restrict__ out, const float* __restrict__ wp,
           const float* __restrict__ bp, float* __restrict__ I, const float* __restrict__ a_prev,
           int data_grad, uint32_t wait_iters) {
@@ -55,14 +55,15 @@ tc_conv16(const float* __restrict__ in, int C, int H, int W, const float* __rest
   __shared__ uint64_t mma_bar;
   __shared__ uint32_t tmem_slot;
   __shared__ float sb[CP], swp[CP];
+  __shared__ int bail;
   unsigned char* act = sm;                          // [2 planes][kRows][16 B]
   unsigned char* wB = sm + 2 * kPlane;              // [9 taps][2 planes][16 rows][16 B]
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int n = blockIdx.z, x0 = blockIdx.x * TW, y0 = blockIdx.y * TH;
   const int64_t hw = (int64_t)H * W;
-  const float* src = in + (int64_t)n * C * hw;
+  const int tiles_x = (W + TW - 1) / TW, tiles_y = (H + TH - 1) / TH;
+  const int64_t ntiles = (int64_t)N * tiles_x * tiles_y;
 
-  // ---- operands: weights as B[n][k] per tap, the input tile as A rows
+  // ---- once per CTA: weights as B[n][k] per tap, TMEM, the MMA barrier
   for (int i = tid; i < 9 * 2 * CP * 8; i += kThreads) {
     const int e = i % 8, r = (i / 8) % CP, col = (i / (8 * CP)) % 2, t = i / (8 * CP * 2);
     const int k = 8 * col + e;                      // K index (input channel of the GEMM)
@@ -76,87 +77,108 @@ tc_conv16(const float* __restrict__ in, int C, int H, int W, const float* __rest
     sb[tid] = (!data_grad && tid < C) ? b[tid] : 0.0f;
     swp[tid] = (I && tid < C) ? wp[tid] : 0.0f;
   }
-  for (int r = tid; r < kRows; r += kThreads) {
-    const int p = r - kLead;                        // grid position of this row
-    float v[CP];
-    const int py = p / Wp, px = p - py * Wp;
-    const int gx = x0 - 1 + px, gy = y0 - 1 + py;
-    const bool inside = p >= 0 && p < Hp * Wp && gx >= 0 && gx < W && gy >= 0 && gy < H;
-#pragma unroll
-    for (int c = 0; c < CP; ++c)
-      v[c] = (inside && c < C) ? __ldg(src + (int64_t)c * hw + (int64_t)gy * W + gx) : 0.0f;
-    __align__(16) __nv_bfloat162 h[CP / 2];
-#pragma unroll
-    for (int c = 0; c < CP / 2; ++c) h[c] = __floats2bfloat162_rn(v[2 * c], v[2 * c + 1]);
-    *reinterpret_cast<uint4*>(act + r * 16) = reinterpret_cast<const uint4*>(h)[0];
-    *reinterpret_cast<uint4*>(act + kPlane + r * 16) = reinterpret_cast<const uint4*>(h)[1];
-  }
+  if (tid == 0) bail = 0;
   if (warp == 0) tmem_alloc(&tmem_slot, kTmemCols);
   if (tid == 0) mbar_init(&mma_bar, 1);
-  fence_proxy_async_smem();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
+  uint32_t phase = 0;
 
-  // ---- 9 MMAs per block of 128 grid positions, one thread issues them all
-  if (tid == 0) {
-    const uint32_t abase = smem_u32(act), bbase = smem_u32(wB);
-    const uint32_t idesc = umma_idesc_bf16(128, CP);
-    for (int blk = 0; blk < kNB; ++blk) {
-      const int m0 = kLead + kMStart + blk * 128;
-      for (int t = 0; t < 9; ++t) {
-        const uint64_t ad = umma_desc(abase + (uint32_t)(m0 + tap_offset(t)) * 16, kPlane, 128);
-        const uint64_t bd = umma_desc(bbase + t * (2 * CP * 16), CP * 16, 128);
-        umma_bf16(tmem + blk * CP, ad, bd, idesc, t != 0);
-      }
+  // ---- persistent loop over (image, tile)
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int n = (int)(tile / (tiles_x * tiles_y));
+    const int tt = (int)(tile % (tiles_x * tiles_y));
+    const int x0 = (tt % tiles_x) * TW, y0 = (tt / tiles_x) * TH;
+    const float* src = in + (int64_t)n * C * hw;
+    // the input tile as A rows (zero outside the image and in the padding rows)
+    for (int r = tid; r < kRows; r += kThreads) {
+      const int p = r - kLead;                      // grid position of this row
+      float v[CP];
+      const int py = p / Wp, px = p - py * Wp;
+      const int gx = x0 - 1 + px, gy = y0 - 1 + py;
+      const bool inside = p >= 0 && p < Hp * Wp && gx >= 0 && gx < W && gy >= 0 && gy < H;
+#pragma unroll
+      for (int c = 0; c < CP; ++c)
+        v[c] = (inside && c < C) ? __ldg(src + (int64_t)c * hw + (int64_t)gy * W + gx) : 0.0f;
+      __align__(16) __nv_bfloat162 h[CP / 2];
+#pragma unroll
+      for (int c = 0; c < CP / 2; ++c) h[c] = __floats2bfloat162_rn(v[2 * c], v[2 * c + 1]);
+      *reinterpret_cast<uint4*>(act + r * 16) = reinterpret_cast<const uint4*>(h)[0];
+      *reinterpret_cast<uint4*>(act + kPlane + r * 16) = reinterpret_cast<const uint4*>(h)[1];
     }
-    umma_commit(&mma_bar);
-  }
-  // every thread of the CTA takes the same branch below (tcgen05.ld is warp-wide)
-  const bool ok = __syncthreads_and(mbar_wait(&mma_bar, 0, wait_iters) ? 1 : 0) != 0;
-  tc_fence_after();
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
 
-  // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) of blocks w / 4 and w / 4 + 2
-  const float* prev = data_grad ? a_prev + (int64_t)n * C * hw : nullptr;
-  float* dst = out + (int64_t)n * C * hw;
-  for (int blk = warp >> 2; blk < kNB; blk += 2) {
-    const int m = kMStart + blk * 128 + (warp & 3) * 32 + lane;
-    float acc[CP];
-    if (ok) tmem_ld16(tmem + ((uint32_t)((warp & 3) * 32) << 16) + blk * CP, acc);
-    const int py = m / Wp, px = m - py * Wp;
-    const int gx = x0 - 1 + px, gy = y0 - 1 + py;
-    const bool valid = py >= 1 && py <= TH && px >= 1 && px <= TW && gx < W && gy < H;
-    if (!valid) continue;
-    const int64_t g = (int64_t)gy * W + gx;
-    if (!ok) {
-      // the MMAs did not complete within the bound: the outputs are NaN
-      for (int c = 0; c < C; ++c) dst[(int64_t)c * hw + g] = __int_as_float(0x7fc00000);
-      if (I && !data_grad) I[(int64_t)n * hw + g] = __int_as_float(0x7fc00000);
-      continue;
-    }
-    if (data_grad) {
-#pragma unroll
-      for (int c = 0; c < CP; ++c) {
-        if (c >= C) break;
-        const int64_t o = (int64_t)c * hw + g;
-        dst[o] = prev[o] > 0.0f ? acc[c] : 0.0f;
+    // 9 MMAs per block of 128 grid positions, one thread issues them all
+    if (tid == 0) {
+      const uint32_t abase = smem_u32(act), bbase = smem_u32(wB);
+      const uint32_t idesc = umma_idesc_bf16(128, CP);
+      for (int blk = 0; blk < kNB; ++blk) {
+        const int m0 = kLead + kMStart + blk * 128;
+        for (int t = 0; t < 9; ++t) {
+          const uint64_t ad = umma_desc(abase + (uint32_t)(m0 + tap_offset(t)) * 16, kPlane, 128);
+          const uint64_t bd = umma_desc(bbase + t * (2 * CP * 16), CP * 16, 128);
+          umma_bf16(tmem + blk * CP, ad, bd, idesc, t != 0);
+        }
       }
-    } else {
-      float Iv = I ? bp[0] : 0.0f;
-#pragma unroll
-      for (int c = 0; c < CP; ++c) {
-        if (c >= C) break;
-        const float a = fmaxf(acc[c] + sb[c], 0.0f);
-        dst[(int64_t)c * hw + g] = a;
-        Iv += swp[c] * a;
-      }
-      if (I) I[(int64_t)n * hw + g] = Iv;
+      umma_commit(&mma_bar);
     }
-  }
-  if (!ok && tid == 0) {
-    // still in flight after the bound: wait (again bounded) before freeing TMEM
-    mbar_wait(&mma_bar, 0, kDrainIters);
+    // every thread of the CTA takes the same branch below (tcgen05.ld is warp-wide)
+    const bool ok = __syncthreads_and(mbar_wait(&mma_bar, phase, wait_iters) ? 1 : 0) != 0;
+    phase ^= 1u;
+    tc_fence_after();
+
+    // epilogue: warp w reads TMEM lanes 32 (w % 4) of blocks w / 4 and w / 4 + 2
+    const float* prev = data_grad ? a_prev + (int64_t)n * C * hw : nullptr;
+    float* dst = out + (int64_t)n * C * hw;
+    for (int blk = warp >> 2; blk < kNB; blk += 2) {
+      const int m = kMStart + blk * 128 + (warp & 3) * 32 + lane;
+      float acc[CP];
+      if (ok) tmem_ld16(tmem + ((uint32_t)((warp & 3) * 32) << 16) + blk * CP, acc);
+      const int py = m / Wp, px = m - py * Wp;
+      const int gx = x0 - 1 + px, gy = y0 - 1 + py;
+      const bool valid = py >= 1 && py <= TH && px >= 1 && px <= TW && gx < W && gy < H;
+      if (!valid) continue;
+      const int64_t g = (int64_t)gy * W + gx;
+      if (!ok) {
+        // the MMAs did not complete within the bound: the outputs are NaN
+        for (int c = 0; c < C; ++c) dst[(int64_t)c * hw + g] = __int_as_float(0x7fc00000);
+        if (I && !data_grad) I[(int64_t)n * hw + g] = __int_as_float(0x7fc00000);
+        continue;
+      }
+      if (data_grad) {
+#pragma unroll
+        for (int c = 0; c < CP; ++c) {
+          if (c >= C) break;
+          const int64_t o = (int64_t)c * hw + g;
+          dst[o] = prev[o] > 0.0f ? acc[c] : 0.0f;
+        }
+      } else {
+        float Iv = I ? bp[0] : 0.0f;
+#pragma unroll
+        for (int c = 0; c < CP; ++c) {
+          if (c >= C) break;
+          const float a = fmaxf(acc[c] + sb[c], 0.0f);
+          dst[(int64_t)c * hw + g] = a;
+          Iv += swp[c] * a;
+        }
+        if (I) I[(int64_t)n * hw + g] = Iv;
+      }
+    }
+    if (!ok && tid == 0) {
+      // still in flight after the bound: wait (again bounded) before the operands
+      // and the accumulators are reused; give up on the launch if that fails too
+      if (!mbar_wait(&mma_bar, phase ^ 1u, kDrainIters)) bail = 1;
+    }
+    // the next tile rewrites the operands and the accumulators
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (bail) break;
   }
   tc_fence_before();
   __syncthreads();
@@ -317,14 +339,38 @@ tc_wgrad16(const float* __restrict__ dz, const float* __restrict__ act, int N, i
 
 }  // namespace
 
+// CTAs of 256 threads a persistent tensor-core kernel can keep on one SM:
+// bounded by threads, registers, shared memory (with the static part and the
+// per-CTA reservation) and TMEM columns (512 per SM)
+static int resident_ctas(const void* kern, size_t dyn_smem, uint32_t tmem_cols, int* per_sm, int* nsm) {
+  int dev = 0, sm_smem = 0, sm_regs = 0;
+  cudaFuncAttributes fa{};
+  ET_CHECK_CUDA(cudaGetDevice(&dev));
+  ET_CHECK_CUDA(cudaDeviceGetAttribute(nsm, cudaDevAttrMultiProcessorCount, dev));
+  ET_CHECK_CUDA(cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+  ET_CHECK_CUDA(cudaDeviceGetAttribute(&sm_regs, cudaDevAttrMaxRegistersPerMultiprocessor, dev));
+  ET_CHECK_CUDA(cudaFuncGetAttributes(&fa, kern));
+  ET_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+  int n = 2048 / kThreads;
+  n = std::min(n, sm_regs / std::max(1, fa.numRegs * kThreads));
+  n = std::min(n, sm_smem / (int)(dyn_smem + fa.sharedSizeBytes + 1024));
+  n = std::min(n, (int)(512 / tmem_cols));
+  *per_sm = std::max(n, 1);
+  return ET_OK;
+}
+
 int et_train_tc_conv(const float* in, int N, int C, int H, int W, const float* w, const float* b,
                      float* out, const float* wp, const float* bp, float* I, const float* a_prev,
                      bool data_grad, cudaStream_t stream) {
   if (C < 1 || C > CP) return ET_ERR_UNIMPLEMENTED;
   const size_t smem = 2 * (size_t)kPlane + kWB;
   ET_CHECK_CUDA(cudaFuncSetAttribute(tc_conv16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  dim3 grid((W + TW - 1) / TW, (H + TH - 1) / TH, N);
-  tc_conv16<<<grid, kThreads, smem, stream>>>(in, C, H, W, w, b, out, wp, bp, I, a_prev, data_grad ? 1 : 0,
+  int per_sm = 0, nsm = 0;
+  const int rc = resident_ctas(reinterpret_cast<const void*>(tc_conv16), smem, kTmemCols, &per_sm, &nsm);
+  if (rc != ET_OK) return rc;
+  const int64_t tiles = (int64_t)N * ((W + TW - 1) / TW) * ((H + TH - 1) / TH);
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)nsm * per_sm));
+  tc_conv16<<<grid, kThreads, smem, stream>>>(in, N, C, H, W, w, b, out, wp, bp, I, a_prev, data_grad ? 1 : 0,
                                               et_tc_wait_iters());
   ET_CHECK_LAUNCH();
   return ET_OK;
@@ -335,14 +381,9 @@ int et_train_tc_wgrad(const float* dz, const float* act, int N, int C, int H, in
   if (C < 1 || C > CP) return ET_ERR_UNIMPLEMENTED;
   const size_t smem = (size_t)kAbytes + kBbytes + sizeof(float) * CP * ((WTH + 2) * (WTW + 2) + WTH * WTW);
   ET_CHECK_CUDA(cudaFuncSetAttribute(tc_wgrad16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int dev = 0, nsm = 0, sm_smem = 0;
-  ET_CHECK_CUDA(cudaGetDevice(&dev));
-  ET_CHECK_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  ET_CHECK_CUDA(cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
-  // persistent CTAs: as many per SM as the shared memory holds (plus the static
-  // part and the per-CTA reservation), at most 8 of 256 threads; TMEM (32 of
-  // 512 columns each) is not the limit
-  const int per_sm = std::min(8, sm_smem / (int)(smem + 2048));
+  int per_sm = 0, nsm = 0;
+  const int rc = resident_ctas(reinterpret_cast<const void*>(tc_wgrad16), smem, kWTmemCols, &per_sm, &nsm);
+  if (rc != ET_OK) return rc;
   const int64_t tiles = (int64_t)N * ((W + WTW - 1) / WTW) * ((H + WTH - 1) / WTH);
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)nsm * std::max(per_sm, 1)));
   tc_wgrad16<<<grid, kThreads, smem, stream>>>(dz, act, N, C, H, W, gw, gb, et_tc_wait_iters());
