@@ -4,7 +4,8 @@
 // tcgen05 with BF16 operands and FP32 accumulation in TMEM.  Layer 0, BiLIF
 // and the loss stay in FP32 on the CUDA cores (train.cu).
 //
-// One CTA computes a 32 x 15 output tile of one image.  The input tile with a
+// Persistent CTAs (weights staged, TMEM allocated once) walk 32 x 15 output
+// tiles of the images.  The input tile with a
 // one-pixel halo (34 x 17 positions) is converted to BF16 into the K-major,
 // no-swizzle operand layout: two planes of 16-byte rows, plane 0 holding
 // channels 0-7 and plane 1 channels 8-15 of every position of the padded grid
