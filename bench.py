@@ -16,7 +16,6 @@ host buffers, and the CPU oracle timed on the host cores.
 """
 import argparse
 import json
-import math
 import os
 import statistics
 import subprocess

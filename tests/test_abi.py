@@ -3,7 +3,6 @@ declares (no compute calls: this runs without a GPU)."""
 import os
 import re
 
-import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 

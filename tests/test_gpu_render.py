@@ -16,7 +16,6 @@ alpha = 0.05 amplifies direction rounding by d ln D / d theta ~ 4 / alpha^2
 ~ 1600, i.e. 6e-8 -> 1e-4 relative per glossy bounce.  So every agreeing pixel
 must be within 2e-3 |ref| + 1e-6, and at least 99.9 % of them within the strict
 1e-4 |ref| + 1e-7."""
-import math
 
 import numpy as np
 import pytest
