@@ -238,26 +238,44 @@ tc_wgrad16(const float* __restrict__ dz, const float* __restrict__ act, int N, i
   const uint32_t idesc = umma_idesc_bf16(128, CP);
   uint32_t phase = 0;
   bool first = true;
-  for (int64_t tile = blockIdx.x; tile < ntiles && !bail; tile += gridDim.x) {
+  // the FP32 tiles of the next tile are loaded into registers while the
+  // current one is converted and multiplied: activations with a one-pixel halo
+  // [ci][10][18] and dz [co][8][16], element i = tid + j * kThreads
+  constexpr int kSa = CP * (WTH + 2) * (WTW + 2), kSd = CP * WTH * WTW;
+  constexpr int kRa = (kSa + kThreads - 1) / kThreads, kRd = kSd / kThreads;
+  static_assert(kSd % kThreads == 0, "dz tile elements per thread");
+  float ra[kRa], rd[kRd];
+  auto fetch = [&](int64_t tile) {
     const int n = (int)(tile / (tiles_x * tiles_y));
     const int tt = (int)(tile % (tiles_x * tiles_y));
     const int x0 = (tt % tiles_x) * WTW, y0 = (tt / tiles_x) * WTH;
     const float* a_n = act + (int64_t)n * C * hw;
     const float* d_n = dz + (int64_t)n * C * hw;
-    // stage the FP32 tiles with coalesced loads: activations with a one-pixel
-    // halo [ci][10][18], dz [co][8][16]
-    for (int i = tid; i < CP * (WTH + 2) * (WTW + 2); i += kThreads) {
+#pragma unroll
+    for (int j = 0; j < kRa; ++j) {
+      const int i = tid + j * kThreads;
       const int c = i / ((WTH + 2) * (WTW + 2)), r = i % ((WTH + 2) * (WTW + 2));
       const int y = y0 - 1 + r / (WTW + 2), x = x0 - 1 + r % (WTW + 2);
-      sa[i] = (c < C && y >= 0 && y < H && x >= 0 && x < W) ? __ldg(a_n + (int64_t)c * hw + (int64_t)y * W + x)
-                                                           : 0.0f;
+      ra[j] = (i < kSa && c < C && y >= 0 && y < H && x >= 0 && x < W)
+                  ? __ldg(a_n + (int64_t)c * hw + (int64_t)y * W + x) : 0.0f;
     }
-    for (int i = tid; i < CP * WTH * WTW; i += kThreads) {
+#pragma unroll
+    for (int j = 0; j < kRd; ++j) {
+      const int i = tid + j * kThreads;
       const int c = i / (WTH * WTW), r = i % (WTH * WTW);
       const int y = y0 + r / WTW, x = x0 + r % WTW;
-      sd[i] = (c < C && y < H && x < W) ? __ldg(d_n + (int64_t)c * hw + (int64_t)y * W + x) : 0.0f;
+      rd[j] = (c < C && y < H && x < W) ? __ldg(d_n + (int64_t)c * hw + (int64_t)y * W + x) : 0.0f;
     }
+  };
+  if (blockIdx.x < ntiles) fetch(blockIdx.x);
+  for (int64_t tile = blockIdx.x; tile < ntiles && !bail; tile += gridDim.x) {
+#pragma unroll
+    for (int j = 0; j < kRa; ++j)
+      if (tid + j * kThreads < kSa) sa[tid + j * kThreads] = ra[j];
+#pragma unroll
+    for (int j = 0; j < kRd; ++j) sd[tid + j * kThreads] = rd[j];
     __syncthreads();
+    if (tile + gridDim.x < ntiles) fetch(tile + gridDim.x);
     // A pieces: (chunk kc, row m = t * 16 + ci) = 8 consecutive x of channel ci,
     // shifted by tap t
     for (int i = tid; i < kChunks * kArows; i += kThreads) {
