@@ -350,7 +350,9 @@ int et_evsnet_train_backward(const float* logl, const et_train_shape* shape,
  * (see et_train_workspace_bytes) are rejected with ET_ERR_CAPACITY.  The call
  * itself allocates nothing.  The first call on a device looks up the array's
  * device address (that device must be current); make that first call before
- * any stream capture begins.  All calls share the one array and it keeps the
+ * any stream capture begins.  The address is tied to the context it was looked
+ * up in: after cudaDeviceReset (a new primary context) the next call looks it
+ * up again, so that call too should come before any capture.  All calls share the one array and it keeps the
  * previous call's contents (the call clears what must start at zero), so two
  * calls whose execution overlaps on the GPU -- e.g. on different streams --
  * race and give wrong gradients: serialise them.  Results, errors and the

@@ -19,6 +19,7 @@
 // is differentiated (not detached).
 #include <algorithm>
 #include <mutex>
+#include <cuda.h>
 #include "et_internal.cuh"
 #include "evsnet_common.h"
 #include "train_api.h"
@@ -803,7 +804,42 @@ namespace {
 constexpr size_t kStaticWorkspaceBytes = (size_t)32 << 20;   // 32 MiB
 constexpr int kMaxDevices = 64;
 std::mutex g_static_ws_mutex;
-void* g_static_ws[kMaxDevices] = {};
+// Per device: the array's device address and the unique id of the context it
+// was looked up in.  A module's __device__ arrays live in one context; after
+// cudaDeviceReset (or any teardown of the primary context) the next context
+// loads the module again and the array may sit elsewhere, so the address is
+// looked up again whenever the current context's id differs.
+struct StaticWs {
+  void* ptr;
+  unsigned long long ctx_id;
+};
+StaticWs g_static_ws[kMaxDevices] = {};
+// Driver calls reached through the runtime's entry-point query (the library
+// links only the runtime).
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
+
+// Id of the calling thread's current context; 0 if none is current yet.
+int current_context_id(unsigned long long* id) {
+  *id = 0;
+  if (!g_ctx_get_current || !g_ctx_get_id) {
+    cudaDriverEntryPointQueryResult q1, q2;
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+        q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+      return ET_ERR_CUDA;
+    g_ctx_get_current = (CtxGetCurrentFn)f1;
+    g_ctx_get_id = (CtxGetIdFn)f2;
+  }
+  CUcontext ctx = nullptr;
+  if (g_ctx_get_current(&ctx) != CUDA_SUCCESS) return ET_ERR_CUDA;
+  if (ctx && g_ctx_get_id(ctx, id) != CUDA_SUCCESS) return ET_ERR_CUDA;
+  return ET_OK;
+}
 }  // namespace
 
 // Device memory; host code must not use this name as an address (on the host it
@@ -833,14 +869,22 @@ extern "C" int et_evsnet_train_backward_static(const float* logl, const et_train
   if (dev < 0 || dev >= kMaxDevices) return ET_ERR_ARG;
   void* base = nullptr;
   {
-    // first call on this device (with it current): look up the array's device address
+    // first call on this device (with it current), or first call in a new
+    // context of it: look up the array's device address
     std::lock_guard<std::mutex> lock(g_static_ws_mutex);
-    if (!g_static_ws[dev]) {
+    unsigned long long id = 0;
+    rc = current_context_id(&id);
+    if (rc != ET_OK) return rc;
+    if (!g_static_ws[dev].ptr || id == 0 || g_static_ws[dev].ctx_id != id) {
       void* p = nullptr;
       ET_CHECK_CUDA(cudaGetSymbolAddress(&p, g_static_workspace));
-      g_static_ws[dev] = p;
+      // the lookup makes the device's primary context current if none was
+      rc = current_context_id(&id);
+      if (rc != ET_OK) return rc;
+      g_static_ws[dev].ptr = p;
+      g_static_ws[dev].ctx_id = id;
     }
-    base = g_static_ws[dev];
+    base = g_static_ws[dev].ptr;
   }
   // the backward clears the part of the scratch that must start at zero (the
   // carried membrane gradient of the spatial form) and overwrites the rest
