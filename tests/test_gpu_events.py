@@ -138,9 +138,15 @@ def test_evsnet_paper_form_kernel7_residual(api, orc):
     assert len(oev) > 50
 
 
-def test_identity_evsnet_equals_gpu_threshold(api, orc):
+@pytest.mark.parametrize("form", [(0, 2, 2, 1, 3), (0, 4, 16, 1, 3), (1, 7, 16, 7, 1), (1, 7, 2, 7, 1)],
+                         ids=["3x3_L2_C2", "3x3_L4_C16", "temporal_k7_M3_C16", "temporal_k7_M3_C2"])
+def test_identity_evsnet_equals_gpu_threshold(api, orc, form):
     """P6: the hand-set identity network with beta = 1, Vth = reset = C reproduces
-    the threshold generator while steps stay below C."""
+    the threshold generator while steps stay below C -- for stacks of 3x3
+    convolutions and for the paper's temporal form (kernel 7 along time, three
+    residual blocks with zero branches), whose events must equal the threshold
+    generator's bit for bit on every pixel whose potential never came within
+    1e-5 of the threshold."""
     C = 0.2
     rng = np.random.default_rng(4)
     F, H, W = 40, 33, 35
@@ -150,7 +156,7 @@ def test_identity_evsnet_equals_gpu_threshold(api, orc):
     dl = torch.as_tensor(lf).cuda()
     ref = torch.zeros(H * W, dtype=torch.float64, device="cuda")
     thr = api.threshold_events(dl, C, ref, False).host()
-    d = inputs.identity_evsnet(0, 2, 2, 1, 3, vth=C)
+    d = inputs.identity_evsnet(*form, vth=C)
     onet = _net(orc, d)
     _, _, mg = orc.evsnet_forward(lf, onet, orc.EvsState.new(onet, H, W), want_margin=True)
     gnet = api.EvsNetDev.from_dict(d)
