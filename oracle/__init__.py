@@ -58,9 +58,9 @@ def lib():
         L.orc_logl.argtypes = [P, i64, i32, C.c_double, P]
         L.orc_threshold_events.argtypes = [P, i32, i32, i32, C.c_double, i32, P, P, P, i64]
         L.orc_threshold_events.restype = i64
-        L.orc_evsnet_forward.argtypes = [P, i32, i32, i32, i32, i32, i32, i32, i32, C.c_double,
-                                         C.c_double, C.c_double, P, P, i32, P, P, P, P, P, i64,
-                                         P, P, i32]
+        L.orc_evsnet_forward.argtypes = [P, i32, i32, i32, i32, i32, i32, i32, i32, i32, i32,
+                                         C.c_double, C.c_double, C.c_double, P, P, i32, P, P, P,
+                                         P, P, i64, P, P, i32]
         L.orc_evsnet_forward.restype = i64
         L.orc_sensor_events.argtypes = [P, i32, i32, i32, C.c_double, C.c_double, C.c_double,
                                         C.c_double, C.c_double, C.c_double, C.c_uint64, i32, P,
@@ -337,20 +337,37 @@ class EvsNet:
     reset: float
     w: np.ndarray      # flat float64
     b: np.ndarray      # flat float64
+    ks0: int = 0       # > 0: layer 0 is a one-step ks0 x ks0 spatial convolution (a stem)
+    delay: int = 0     # events of step k are labelled t0 + k - delay
+
+    @staticmethod
+    def from_dict(d):
+        """From a weights dictionary (keys as in the package's inputs module)."""
+        return EvsNet(int(d["kind"]), int(d["n_layers"]), int(d["C"]), int(d["kt"]), int(d["ks"]),
+                      float(d["beta"]), float(d["vth"]), float(d["reset"]),
+                      np.asarray(d["w"], np.float64), np.asarray(d["b"], np.float64),
+                      int(d.get("ks0", 0)), int(d.get("delay", 0)))
+
+    def layer_shape(self, i):
+        """(Cin, kt, ks) of conv layer i."""
+        if i == 0:
+            return (1, 1, self.ks0) if self.ks0 > 0 else (1, self.kt, self.ks)
+        return self.C, self.kt, self.ks
 
     def n_weights(self):
         n = 0
         for i in range(self.n_layers):
-            n += self.C * (1 if i == 0 else self.C) * self.kt * self.ks * self.ks
+            cin, kt, ks = self.layer_shape(i)
+            n += self.C * cin * kt * ks * ks
         return n + self.C
 
     def layer_weights(self):
         """list of (W [Cout,Cin,kt,ks,ks], b [Cout]) plus the projection (W [C], b [1])."""
         out, wo, bo = [], 0, 0
         for i in range(self.n_layers):
-            cin = 1 if i == 0 else self.C
-            n = self.C * cin * self.kt * self.ks * self.ks
-            out.append((self.w[wo:wo + n].reshape(self.C, cin, self.kt, self.ks, self.ks),
+            cin, kt, ks = self.layer_shape(i)
+            n = self.C * cin * kt * ks * ks
+            out.append((self.w[wo:wo + n].reshape(self.C, cin, kt, ks, ks),
                         self.b[bo:bo + self.C]))
             wo += n
             bo += self.C
@@ -393,7 +410,8 @@ def evsnet_forward(logl_frames, net: EvsNet, state: EvsState, t0=0, want_I=False
         if mg is not None:
             mg[:] = np.inf
         n = lib().orc_evsnet_forward(_p(lf), F, H, W, net.kind, net.n_layers, net.C, net.kt,
-                                     net.ks, net.beta, net.vth, net.reset, _p(w), _p(b), t0,
+                                     net.ks, net.ks0, net.delay, net.beta, net.vth, net.reset,
+                                     _p(w), _p(b), t0,
                                      _p(V), _p(hist), _p(last), C.byref(ini), _p(ev), cap,
                                      _p(I), _p(mg), nthreads)
         if n <= cap:
@@ -508,11 +526,12 @@ def torch_forward(X, net: EvsNet, params=None, smooth=False, alpha=2.0, V0=None)
     F = torch.nn.functional
     B, K, H, W = X.shape
     layers, (wp, bp) = params if params is not None else torch_params(net)
-    pad = net.ks // 2
 
     def conv(h, Wt, bt):
-        # h [B, Cin, K, H, W]; causal in time, zero-padded in space
-        h = F.pad(h, (pad, pad, pad, pad, net.kt - 1, 0))
+        # h [B, Cin, K, H, W]; causal in time, zero-padded in space (the
+        # kernel's own extent: a stem layer 0 is one step by ks0 x ks0)
+        kt, pad = Wt.shape[2], Wt.shape[3] // 2
+        h = F.pad(h, (pad, pad, pad, pad, kt - 1, 0))
         return F.conv3d(h, Wt, bt)
 
     x = X.unsqueeze(1)

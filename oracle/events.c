@@ -72,6 +72,12 @@ int64_t orc_threshold_events(const float* logl, int F, int H, int W, double C, i
  * kt-1 steps back; steps before the start of the clip contribute zero.
  * hist: [n_layers][kt-1][C][H][W], the input of each layer at the last kt-1
  * steps (slot kt-2 = previous step); only channel 0 is used for layer 0.
+ * Spatial stem (ks0 > 0): layer 0 is instead a one-step ks0 x ks0 spatial
+ * convolution of the current X, W[C][1][1][ks0][ks0] (zero padding); its
+ * history slots are unused.  ks0 = 0: layer 0 has the kt x ks x ks shape.
+ * Delay: the events of step k carry t = t0 + k - delay (a centred window
+ * labels its output with the window's centre); steps whose label would be
+ * negative emit nothing.
  */
 static void conv_layer(const double* in, const double* hist, int Cin, int Cout, int C,
                        int kt, int ks, int H, int W, const double* w, const double* b,
@@ -109,10 +115,10 @@ static void push_hist(double* hist, const double* in, int Cin, int C, int kt, in
 }
 
 int64_t orc_evsnet_forward(const float* logl, int F, int H, int W, int kind, int n_layers,
-                           int C, int kt, int ks, double beta, double vth, double reset,
-                           const double* w, const double* b, int t0, double* V, double* hist,
-                           double* last_l, int* initialized, int32_t* events, int64_t cap,
-                           double* I_out, double* margin, int nthreads) {
+                           int C, int kt, int ks, int ks0, int delay, double beta, double vth,
+                           double reset, const double* w, const double* b, int t0, double* V,
+                           double* hist, double* last_l, int* initialized, int32_t* events,
+                           int64_t cap, double* I_out, double* margin, int nthreads) {
 #ifdef _OPENMP
   if (nthreads > 0) omp_set_num_threads(nthreads);
 #endif
@@ -121,10 +127,12 @@ int64_t orc_evsnet_forward(const float* logl, int F, int H, int W, int kind, int
   /* per-layer weight / bias offsets */
   int64_t woff[64], boff[64];
   int64_t wo = 0, bo = 0;
+  const int kt0 = ks0 > 0 ? 1 : kt, ks0e = ks0 > 0 ? ks0 : ks;   /* layer 0's shape */
   for (int i = 0; i < n_layers; ++i) {
     int cin = i == 0 ? 1 : C;
     woff[i] = wo; boff[i] = bo;
-    wo += (int64_t)C * cin * kt * ks * ks; bo += C;
+    wo += i == 0 ? (int64_t)C * kt0 * ks0e * ks0e : (int64_t)C * cin * kt * ks * ks;
+    bo += C;
   }
   const double* wp = w + wo;
   const double* bp = b + bo;
@@ -146,8 +154,8 @@ int64_t orc_evsnet_forward(const float* logl, int F, int H, int W, int kind, int
       last_l[q] = l;
     }
     /* encoder */
-    conv_layer(x, hist, 1, C, C, kt, ks, H, W, w + woff[0], b + boff[0], h);
-    push_hist(hist, x, 1, C, kt, npix);
+    conv_layer(x, hist, 1, C, C, kt0, ks0e, H, W, w + woff[0], b + boff[0], h);
+    if (kt0 > 1) push_hist(hist, x, 1, C, kt, npix);
     for (int64_t i = 0; i < C * npix; ++i) h[i] = h[i] > 0.0 ? h[i] : 0.0;
     if (kind == 0) {
       for (int l = 1; l < n_layers; ++l) {
@@ -178,10 +186,10 @@ int64_t orc_evsnet_forward(const float* logl, int F, int H, int W, int kind, int
         if (m < margin[q]) margin[q] = m;
       }
       V[q] = vp - reset * S;
-      if (S != 0) {
+      if (S != 0 && (int64_t)t0 + f - delay >= 0) {
         if (nev < cap) {
           events[4*nev] = (int32_t)(q % W); events[4*nev+1] = (int32_t)(q / W);
-          events[4*nev+2] = t0 + f; events[4*nev+3] = S;
+          events[4*nev+2] = t0 + f - delay; events[4*nev+3] = S;
         }
         ++nev;
       }

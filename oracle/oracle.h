@@ -71,10 +71,10 @@ int64_t orc_threshold_events(const float* logl, int F, int H, int W, double C, i
 
 /* EvSNet forward (Eq. 5-6 with Eq. 2-3 BiLIF).  See events.c for the layer packing. */
 int64_t orc_evsnet_forward(const float* logl, int F, int H, int W, int kind, int n_layers,
-                           int C, int kt, int ks, double beta, double vth, double reset,
-                           const double* w, const double* b, int t0, double* V, double* hist,
-                           double* last_l, int* initialized, int32_t* events, int64_t cap,
-                           double* I_out, double* margin, int nthreads);
+                           int C, int kt, int ks, int ks0, int delay, double beta, double vth,
+                           double reset, const double* w, const double* b, int t0, double* V,
+                           double* hist, double* last_l, int* initialized, int32_t* events,
+                           int64_t cap, double* I_out, double* margin, int nthreads);
 
 /* test hooks: BSDF in a local frame (normal +z); mat5 = {albedo rgb, roughness, type} */
 void orc_bsdf_eval(const double* mat5, const double* wo, const double* wi, int64_t n,

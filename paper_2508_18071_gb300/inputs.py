@@ -257,38 +257,52 @@ def city_path(n_frames=1000, first=0, speed_per_frame=0.01, height=1.7):
 
 
 # -------------------------------------------------------------------- EvSNet
+def layer_shape(net, i):
+    """(Cin, kt, ks) of conv layer i of an EvSNet dictionary: layer 0 of a net
+    with a spatial stem (ks0 > 0) is one step by ks0 x ks0."""
+    ks0 = int(net.get("ks0", 0))
+    if i == 0:
+        return (1, 1, ks0) if ks0 > 0 else (1, net["kt"], net["ks"])
+    return net["C"], net["kt"], net["ks"]
+
+
 def random_evsnet(kind=0, n_layers=2, C=8, kt=1, ks=3, seed=2, std=0.1, beta=1.0,
-                  vth=0.2, reset=None):
+                  vth=0.2, reset=None, ks0=0, delay=0):
     """Random-init EvSNet weights N(0, std) in the packed layout: conv layers in
-    order, each [Cout][Cin][kt][ks][ks] (Cin = 1 for the first), then the
-    projection [C]; biases C per conv layer then 1."""
+    order, each [Cout][Cin][kt][ks][ks] (Cin = 1 for the first; a stem layer 0,
+    ks0 > 0, is [C][1][1][ks0][ks0]), then the projection [C]; biases C per conv
+    layer then 1.  `delay` labels the events of step k with t0 + k - delay."""
     rng = np.random.default_rng(seed)
-    nw = sum(C * (1 if i == 0 else C) * kt * ks * ks for i in range(n_layers)) + C
+    net = {"kind": kind, "n_layers": n_layers, "C": C, "kt": kt, "ks": ks, "ks0": int(ks0),
+           "delay": int(delay), "beta": float(beta), "vth": float(vth),
+           "reset": float(vth if reset is None else reset)}
+    nw = 0
+    for i in range(n_layers):
+        cin, t, k = layer_shape(net, i)
+        nw += C * cin * t * k * k
+    nw += C
     nb = C * n_layers + 1
-    return {
-        "kind": kind, "n_layers": n_layers, "C": C, "kt": kt, "ks": ks,
-        "beta": float(beta), "vth": float(vth), "reset": float(vth if reset is None else reset),
-        "w": rng.normal(0, std, nw).astype(np.float32),
-        "b": rng.normal(0, std, nb).astype(np.float32),
-    }
+    net["w"] = rng.normal(0, std, nw).astype(np.float32)
+    net["b"] = rng.normal(0, std, nb).astype(np.float32)
+    return net
 
 
-def identity_evsnet(kind=0, n_layers=2, C=2, kt=1, ks=3, vth=0.2):
+def identity_evsnet(kind=0, n_layers=2, C=2, kt=1, ks=3, vth=0.2, ks0=0):
     """Hand-set weights whose projection reproduces X exactly: the first layer
     splits X into (ReLU(X), ReLU(-X)) with centre taps (+1, -1), inner layers pass
     channels through (centre-tap identity, or zero residual branches) and the
     projection is (+1, -1)."""
-    net = random_evsnet(kind, n_layers, C, kt, ks, seed=0, vth=vth)
+    net = random_evsnet(kind, n_layers, C, kt, ks, seed=0, vth=vth, ks0=ks0)
     w = np.zeros_like(net["w"])
     b = np.zeros_like(net["b"])
     r = ks // 2
     off = 0
     for i in range(n_layers):
-        cin = 1 if i == 0 else C
-        Wl = np.zeros((C, cin, kt, ks, ks), np.float32)
+        cin, t, k = layer_shape(net, i)
+        Wl = np.zeros((C, cin, t, k, k), np.float32)
         if i == 0:
-            Wl[0, 0, kt - 1, r, r] = 1.0
-            Wl[1, 0, kt - 1, r, r] = -1.0
+            Wl[0, 0, t - 1, k // 2, k // 2] = 1.0
+            Wl[1, 0, t - 1, k // 2, k // 2] = -1.0
         elif kind == 0:
             for c in range(2):
                 Wl[c, c, kt - 1, r, r] = 1.0

@@ -12,8 +12,7 @@ from paper_2508_18071_gb300 import inputs
 
 
 def _net(orc, d):
-    return orc.EvsNet(d["kind"], d["n_layers"], d["C"], d["kt"], d["ks"], d["beta"], d["vth"],
-                      d["reset"], np.asarray(d["w"], np.float64), np.asarray(d["b"], np.float64))
+    return orc.EvsNet.from_dict(d)
 
 
 # ---------------------------------------------------------------- Eq. 1
@@ -155,6 +154,127 @@ def test_evsnet_conv_stack_matches_torch_conv3d(orc, kind, nl, kt, ks, C):
     X = torch.tensor(np.diff(lf.astype(np.float64), axis=0)[None])
     _, _, It, _ = orc.torch_forward(X, net)
     np.testing.assert_allclose(I, It[0].numpy(), rtol=1e-10, atol=1e-12)
+
+
+@pytest.mark.parametrize("kind,nl,kt,ks,C,ks0", [(1, 7, 7, 1, 16, 3), (1, 3, 4, 1, 4, 5),
+                                                 (0, 3, 3, 1, 4, 3), (0, 2, 1, 3, 4, 5)])
+def test_spatial_stem_matches_torch_conv3d(orc, kind, nl, kt, ks, C, ks0):
+    """A spatial stem (layer 0 one step by ks0 x ks0) before temporal or spatial
+    layers: the C loops agree with torch conv3d (a library routine) on I."""
+    torch = pytest.importorskip("torch")
+    d = inputs.random_evsnet(kind, nl, C, kt, ks, seed=8, ks0=ks0)
+    net = _net(orc, d)
+    assert len(net.w) == C * ks0 * ks0 + (nl - 1) * C * C * kt * ks * ks + C
+    lf = inputs.random_logl_clip(6, 12, 9, 11)
+    _, I, _ = orc.evsnet_forward(lf, net, orc.EvsState.new(net, 9, 11), want_I=True)
+    X = torch.tensor(np.diff(lf.astype(np.float64), axis=0)[None])
+    _, _, It, _ = orc.torch_forward(X, net)
+    np.testing.assert_allclose(I, It[0].numpy(), rtol=1e-10, atol=1e-12)
+
+
+def test_centre_tap_stem_equals_current_step_layer0(orc):
+    """A stem whose only non-zero taps are the centre ones computes what the
+    paper form's layer 0 computes when only its current-step taps are non-zero:
+    the two nets then give identical currents (pins the stem's weight offsets)."""
+    C = 6
+    d = inputs.random_evsnet(1, 5, C, 7, 1, seed=4, std=0.3)
+    W0 = d["w"][:C * 7].reshape(C, 7).copy()
+    W0[:, :6] = 0.0
+    d["w"][:C * 7] = W0.ravel()
+    ds = dict(d, ks0=3)
+    stem = np.zeros((C, 3, 3), np.float32)
+    stem[:, 1, 1] = W0[:, 6]
+    ds["w"] = np.concatenate([stem.ravel(), d["w"][C * 7:]])
+    lf = inputs.random_logl_clip(9, 20, 7, 8, step_std=0.3)
+    a, b = _net(orc, d), _net(orc, ds)
+    ea, Ia, _ = orc.evsnet_forward(lf, a, orc.EvsState.new(a, 7, 8), want_I=True)
+    eb, Ib, _ = orc.evsnet_forward(lf, b, orc.EvsState.new(b, 7, 8), want_I=True)
+    np.testing.assert_array_equal(Ia, Ib)
+    assert np.array_equal(orc.sort_events(ea), orc.sort_events(eb))
+
+
+def test_stem_on_spatially_constant_input(orc):
+    """Closed form: on an input that is constant in space, an interior pixel's
+    stem output is X times the sum of the taps (plus the bias) and a corner
+    pixel's is X times the sum of the taps that fall inside the image (zero
+    padding).  Checked with a one-layer stack whose projection is the identity
+    on channel 0."""
+    ks0 = 5
+    d = inputs.random_evsnet(0, 1, 2, 1, 1, seed=3, ks0=ks0, std=0.5)
+    taps = d["w"][:2 * ks0 * ks0].reshape(2, ks0, ks0)
+    taps[0] = np.abs(taps[0])                     # channel 0 stays positive (ReLU inactive)
+    d["w"][:2 * ks0 * ks0] = taps.ravel()
+    d["b"][:] = 0.0
+    d["w"][2 * ks0 * ks0:] = [1.0, 0.0]           # projection: channel 0
+    net = _net(orc, d)
+    H, W = 9, 10
+    lf = np.zeros((3, H, W), np.float32)
+    lf[1] = 0.5
+    lf[2] = 0.75                                   # X = 0.5 then 0.25 everywhere
+    _, I, _ = orc.evsnet_forward(lf, net, orc.EvsState.new(net, H, W), want_I=True)
+    t = taps[0].astype(np.float64)
+    np.testing.assert_allclose(I[0, 4, 5], 0.5 * t.sum(), rtol=1e-14)
+    np.testing.assert_allclose(I[1, 4, 5], 0.25 * t.sum(), rtol=1e-14)
+    np.testing.assert_allclose(I[0, 0, 0], 0.5 * t[2:, 2:].sum(), rtol=1e-14)   # top-left corner
+    np.testing.assert_allclose(I[0, H - 1, W - 1], 0.5 * t[:3, :3].sum(), rtol=1e-14)
+
+
+def test_stem_receptive_field(orc):
+    """An impulse of X at one pixel and step reaches the current of exactly the
+    ks0 x ks0 neighbourhood and, with a one-step stem, 1 + 6 (n_layers - 1)
+    steps for kernel 7 (37 for three residual blocks)."""
+    d = inputs.random_evsnet(1, 7, 4, 7, 1, seed=3, ks0=3)
+    d["w"] = np.abs(d["w"]) + 0.01
+    d["b"] = np.zeros_like(d["b"])
+    net = _net(orc, d)
+    F, H, W = 70, 7, 7
+    lf = np.zeros((F, H, W), np.float32)
+    lf[10:, 3, 3] = 1.0                            # X impulse at step index 9, pixel (3, 3)
+    _, I, _ = orc.evsnet_forward(lf, net, orc.EvsState.new(net, H, W), want_I=True)
+    nzt = np.nonzero(np.abs(I).sum((1, 2)))[0]
+    assert nzt.min() == 9 and nzt.max() == 9 + 36
+    nzs = np.argwhere(np.abs(I).sum(0) > 0)
+    assert set(map(tuple, nzs)) == {(y, x) for y in (2, 3, 4) for x in (2, 3, 4)}
+
+
+def test_delay_labels_events_with_the_window_centre(orc):
+    """delay D: the events of step k carry t0 + k - D, and steps whose label
+    would be negative emit nothing; the dynamics are unchanged."""
+    d = inputs.random_evsnet(1, 3, 4, 5, 1, seed=2, vth=0.2, beta=0.95, ks0=3)
+    lf = inputs.random_logl_clip(3, 30, 6, 7, step_std=0.3)
+    a = _net(orc, d)
+    ea, Ia, _ = orc.evsnet_forward(lf, a, orc.EvsState.new(a, 6, 7), want_I=True)
+    for D, t0 in ((4, 0), (4, 10), (0, 3)):
+        b = _net(orc, dict(d, delay=D))
+        sb = orc.EvsState.new(b, 6, 7)
+        eb, Ib, _ = orc.evsnet_forward(lf, b, sb, t0=t0, want_I=True)
+        np.testing.assert_array_equal(Ia, Ib)
+        want = ea.copy()
+        want[:, 2] += t0 - D
+        want = want[want[:, 2] >= 0]
+        assert len(want) > 20
+        assert np.array_equal(orc.sort_events(eb), orc.sort_events(want))
+
+
+def test_identity_stem_network_equals_threshold_generator(orc):
+    """P6 with a stem: the identity network (centre taps +-1, zero residual
+    branches, projection (+1, -1)) with beta = 1 and Vth = reset = C is the
+    threshold generator while steps stay below C."""
+    C = 0.2
+    rng = np.random.default_rng(11)
+    F, H, W = 40, 6, 7
+    steps = rng.uniform(-0.19, 0.19, (F, H, W))
+    steps[0] = 0
+    lf = (rng.normal(0, 1, (H, W)) + np.cumsum(steps, 0)).astype(np.float32)
+    thr = orc.threshold_events(lf, C, orc.ThresholdState.new(H, W))
+    d = inputs.identity_evsnet(1, 7, 4, 7, 1, vth=C, ks0=3)
+    d["beta"] = 1.0
+    net = _net(orc, d)
+    ev, _, mg = orc.evsnet_forward(lf, net, orc.EvsState.new(net, H, W), want_margin=True)
+    clean = mg > 1e-9
+    keep = lambda e: e[clean[e[:, 1], e[:, 0]]]
+    assert clean.mean() > 0.9 and len(thr) > 50
+    assert np.array_equal(orc.sort_events(keep(ev)), orc.sort_events(keep(thr)))
 
 
 def test_receptive_field_is_43(orc):
@@ -315,6 +435,34 @@ def test_smooth_surrogate_gradient_temporal_residual_form(orc):
         fd = (lp - lm) / (2 * h)
         assert abs(fd - gw[idx]) <= 1e-5 * max(1.0, abs(fd)) + 1e-8, (idx, fd, gw[idx])
     for idx in (0, len(net.b) // 2, len(net.b) - 1):
+        bp_, bm_ = net.b.copy(), net.b.copy()
+        bp_[idx] += h
+        bm_[idx] -= h
+        lp = orc.torch_grads(X, E, orc.EvsNet(**{**net.__dict__, "b": bp_}), smooth=True)[0]
+        lm = orc.torch_grads(X, E, orc.EvsNet(**{**net.__dict__, "b": bm_}), smooth=True)[0]
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - gb[idx]) <= 1e-5 * max(1.0, abs(fd)) + 1e-8
+
+
+def test_smooth_surrogate_gradient_stem_form(orc):
+    """P10 for a spatial stem (3 x 3, one step) before temporal residual blocks:
+    the autograd gradient matches central differences, stem taps included."""
+    d = inputs.random_evsnet(1, 3, 3, 4, 1, seed=6, vth=0.3, beta=0.9, std=0.3, ks0=3)
+    net = _net(orc, d)
+    rng = np.random.default_rng(6)
+    X = rng.normal(0, 0.3, (2, 12, 4, 5))
+    E = rng.choice([-1, 0, 0, 0, 1, 2], X.shape).astype(float)
+    _, gw, gb = orc.torch_grads(X, E, net, smooth=True)
+    h = 1e-6
+    for idx in list(range(0, 27, 4)) + list(rng.choice(np.arange(27, len(net.w)), 6, replace=False)):
+        wp, wm = net.w.copy(), net.w.copy()
+        wp[idx] += h
+        wm[idx] -= h
+        lp = orc.torch_grads(X, E, orc.EvsNet(**{**net.__dict__, "w": wp}), smooth=True)[0]
+        lm = orc.torch_grads(X, E, orc.EvsNet(**{**net.__dict__, "w": wm}), smooth=True)[0]
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - gw[idx]) <= 1e-5 * max(1.0, abs(fd)) + 1e-8, (idx, fd, gw[idx])
+    for idx in (0, 2, len(net.b) - 1):
         bp_, bm_ = net.b.copy(), net.b.copy()
         bp_[idx] += h
         bm_[idx] -= h
