@@ -53,7 +53,7 @@ def lib():
         L.orc_intersect.argtypes = [P, P, P, P, i64, P, P, P, P]
         L.orc_occluded.argtypes = [P, P, P, P, i64, P]
         L.orc_render.argtypes = [P, P, i32, i32, i32, i32, i32, i32, i32, i32, C.c_uint64, P, P,
-                                 i32, P]
+                                 P, i32, P]
         L.orc_render.restype = i32
         L.orc_logl.argtypes = [P, i64, i32, C.c_double, P]
         L.orc_threshold_events.argtypes = [P, i32, i32, i32, C.c_double, i32, P, P, P, i64]
@@ -169,19 +169,24 @@ class Scene:
         return out.astype(bool)
 
     def render(self, cams, W, H, spp, max_depth, seed, first_frame=0, rows=None,
-               records=False, nthreads=0):
-        """Mean radiance per pixel, [F,H,W,3] float64 (rows outside `rows` stay 0)."""
+               records=False, nthreads=0, cond=False):
+        """Mean radiance per pixel, [F,H,W,3] float64 (rows outside `rows` stay 0).
+        records=True adds the per-sample path records; cond=True adds [F,H,W,3]:
+        the smallest light-side cosine, next-event surface cosine and GGX
+        roughness met by the pixel's paths (see oracle.h)."""
         cams = _c(cams, np.float32).reshape(-1, 13)
         F = cams.shape[0]
         y0, y1 = (0, H) if rows is None else rows
         rgb = np.zeros((F, H, W, 3), np.float64)
         rec = np.full((F, H, W, spp, max_depth, 2), -3, np.int32) if records else None
+        cd = np.full((F, H, W, 3), np.inf) if cond else None
         nr = np.zeros(3, np.int64)
         lib().orc_render(self._h, _p(cams), F, first_frame, W, H, y0, y1, spp, max_depth,
-                         C.c_uint64(seed), _p(rgb), _p(rec), nthreads, _p(nr))
+                         C.c_uint64(seed), _p(rgb), _p(rec), _p(cd), nthreads, _p(nr))
         # rays traced (closest + shadow), BVH nodes visited, triangles tested
         self.rays_traced, self.node_visits, self.tri_tests = (int(v) for v in nr)
-        return (rgb, rec) if records else rgb
+        out = (rgb,) + ((rec,) if records else ()) + ((cd,) if cond else ())
+        return out if len(out) > 1 else rgb
 
     def annotations(self, cams, W, H, next_cam=None):
         """Primary-hit annotations through pixel centres: dict of depth [F,H,W],

@@ -53,10 +53,13 @@ void orc_occluded(const orc_scene* s, const double* o, const double* d, const do
 /* cams: [F][13] floats {pos[3], rot[9] row-major camera-to-world, vfov_deg}
  * rgb: [F][H][W][3] double; rows [y0,y1) only.  records (optional):
  * [F][H][W][spp][max_depth][2] int32: (primID of segment b or -1 miss, -2 untraced),
- * (NEE record: 2*light + visible, -1 none). */
+ * (NEE record: 2*light + visible, -1 none).  cond (optional): [F][H][W][3]
+ * double, over the pixel's samples the smallest light-side cosine (emitter hit
+ * after the first segment, or next-event sample), surface-side cosine of a
+ * next-event sample and GGX roughness at a shading point (+inf if none). */
 int orc_render(const orc_scene* s, const float* cams, int F, int first_frame, int W, int H,
                int y0, int y1, int spp, int max_depth, uint64_t seed, double* rgb,
-               int32_t* records, int nthreads, int64_t* work);
+               int32_t* records, double* cond, int nthreads, int64_t* work);
 /* work (optional): [3] = rays traced, BVH nodes visited, triangles tested */
 
 /* Eq. 1: luminance and log map of linear RGB.  mode 0: ln(L + eps); mode 1: the

@@ -443,9 +443,18 @@ static void philox_u(uint32_t pix, uint32_t smp, uint32_t frame, uint32_t w3,
   for (int k = 0; k < 4; ++k) u[k] = u01(o[k]);
 }
 
+/* cond (optional, test infrastructure): the smallest light-side cosine of any
+ * emitter hit or next-event sample, the smallest surface-side cosine of any
+ * next-event sample, and the smallest roughness of any GGX shading point along
+ * the path -- the quantities whose smallness amplifies the kernel's FP32
+ * rounding (updated with min, so a pixel's samples share one record) */
+static void cond_min(double* cond, int i, double v) {
+  if (cond && v < cond[i]) cond[i] = v;
+}
+
 static void trace_sample(const orc_scene* s, const float* cam, int W, int H, int x, int y,
                          int smp, int frame, int max_depth, const uint32_t key[2], double* Lo,
-                         int32_t* rec, int64_t* work) {
+                         int32_t* rec, int64_t* work, double* cond) {
   uint32_t pix = (uint32_t)(y * W + x);
   double u[4];
   philox_u(pix, (uint32_t)smp, (uint32_t)frame, 0u, key, u);
@@ -469,6 +478,7 @@ static void trace_sample(const orc_scene* s, const float* cam, int W, int H, int
       const light_t* lt = &s->lights[m & ~LIGHT_BIT];
       double cosl = -dot3(d, lt->n);
       if (cosl > 0.0) {
+        if (b > 1) cond_min(cond, 0, cosl);
         double w = 1.0;
         if (b > 1) {
           double pl = lt->prob * t * t / (cosl * lt->area);
@@ -490,6 +500,7 @@ static void trace_sample(const orc_scene* s, const float* cam, int W, int H, int
     onb(ng, tt, bt);
     double wol[3] = {dot3(wo, tt), dot3(wo, bt), dot3(wo, ng)};
     const double* mt = s->mats + 8 * (int64_t)m;
+    if ((int)mt[4] == 1) cond_min(cond, 2, mt[3]);
     if (s->n_l > 0) {
       philox_u(pix, (uint32_t)smp, (uint32_t)frame, (uint32_t)(4*b + 1), key, u);
       int j = 0;
@@ -503,6 +514,8 @@ static void trace_sample(const orc_scene* s, const float* cam, int W, int H, int
       double cosi = dot3(wi, ng), cosl = -dot3(wi, lt->n);
       int32_t nrec = -1;
       if (cosi > 0.0 && cosl > 0.0) {
+        cond_min(cond, 0, cosl);
+        cond_min(cond, 1, cosi);
         int vis = !occluded_n(s, on, wi, dist * (1.0 - 1e-4), &work[1], &work[2]);
         ++work[0];
         nrec = 2 * j + vis;
@@ -531,7 +544,7 @@ static void trace_sample(const orc_scene* s, const float* cam, int W, int H, int
 
 int orc_render(const orc_scene* s, const float* cams, int F, int first_frame, int W, int H,
                int y0, int y1, int spp, int max_depth, uint64_t seed, double* rgb,
-               int32_t* records, int nthreads, int64_t* work_out) {
+               int32_t* records, double* cond, int nthreads, int64_t* work_out) {
   uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
   int64_t tot_r = 0, tot_v = 0, tot_t = 0;
   int64_t rows = y1 - y0;
@@ -554,7 +567,9 @@ int orc_render(const orc_scene* s, const float* cams, int F, int first_frame, in
           for (int i = 0; i < 2 * max_depth; ++i) rec[i] = (i % 2 == 0) ? -2 : -1;
         }
         int64_t work[3] = {0, 0, 0};
-        trace_sample(s, cam, W, H, x, y, smp, first_frame + f, max_depth, key, Ls, rec, work);
+        double* cd = cond ? cond + (((int64_t)f * H + y) * W + x) * 3 : NULL;
+        if (cd && smp == 0) cd[0] = cd[1] = cd[2] = INFINITY;
+        trace_sample(s, cam, W, H, x, y, smp, first_frame + f, max_depth, key, Ls, rec, work, cd);
         cr += work[0]; cv += work[1]; ct += work[2];
         for (int k = 0; k < 3; ++k) acc[k] += Ls[k];
       }

@@ -313,3 +313,25 @@ def test_camera_orientation(orc):
     assert frac(prim[1:11, 15], {8, 9}) > 0.6                      # right wall on the right
     assert frac(prim[12:16, 0:6], set(range(10, 20))) > 0.8        # box 1 (x < 0) bottom left
     assert frac(prim[12:16, 10:14], set(range(20, 30))) > 0.8      # box 2 (x > 0) bottom right
+
+
+def test_conditioning_record_of_a_plane_under_a_quad_light(orc):
+    """The optional conditioning record (test infrastructure) leaves the
+    radiance unchanged and holds the path's geometry: for a GGX plane of
+    roughness 0.2 under a parallel quad light at height 1, every next-event
+    sample has light-side cosine h / |p - x| >= 1 / sqrt(1 + r_max^2) and the
+    same surface-side cosine (the two planes are parallel), and the roughness
+    record is 0.2."""
+    s = _plane_light_scene([0.8, 0.8, 0.8, 0.2, 1])
+    sc = _scene(orc, s)
+    target = np.array([0.0, 0.0, -0.3])
+    cams = np.stack([_pixel_camera((0.0, 0.5, 1.0), target)])
+    rgb0 = sc.render(cams, 1, 1, 64, 2, seed=4)
+    rgb, cd = sc.render(cams, 1, 1, 64, 2, seed=4, cond=True)
+    np.testing.assert_array_equal(rgb, rgb0)
+    cosl, cosi, alpha = cd[0, 0, 0]
+    corners = np.array([[-0.3, 1.0, -0.5], [0.3, 1.0, -0.5], [-0.3, 1.0, -0.1], [0.3, 1.0, -0.1]])
+    r_max = max(np.hypot(c[0] - target[0], c[2] - target[2]) for c in corners)
+    assert 1.0 / math.sqrt(1.0 + r_max ** 2) - 1e-3 <= cosl <= 1.0
+    assert abs(cosl - cosi) < 1e-3
+    assert alpha == pytest.approx(0.2, rel=1e-6)
