@@ -43,12 +43,16 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--frames", type=int, default=50, help="frames per step")
     p.add_argument("--spp", type=int, default=2)
-    p.add_argument("--baseline-frames", type=int, default=12)
+    p.add_argument("--baseline-frames", type=int, default=101)
     p.add_argument("--no-baseline", action="store_true")
+    p.add_argument("--no-c2", action="store_true", help="skip the event scores on the procedural scene")
+    p.add_argument("--shard", default="bands", choices=["bands", "frames"],
+                   help="partition across ranks (N > 1): row bands of every frame, or path segments")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-rows", type=int, default=720, help="oracle sample: rows per frame")
     p.add_argument("--cpu-frames", type=int, default=2, help="oracle sample: frames")
-    p.add_argument("--evsnet-dtype", default="bf16", choices=["f32", "bf16", "fp8"])
+    p.add_argument("--evsnet-dtype", default="auto", choices=["auto", "f32", "bf16", "fp8"],
+                   help="auto: BF16 where the network's form has a tensor-core kernel, else FP32")
     p.add_argument("--bvh", default=None, choices=["gpu", "host", "sweep"],
                    help="hierarchy builder (default: the library's)")
     p.add_argument("--no-sweep", action="store_true",
@@ -134,9 +138,7 @@ def cpu_baseline(scene, net_d, spp, rows, frames_for_render=1):
     ys = range(rows)
     t_frame_render = t_r * H_ / rows / frames_for_render
     # EvSNet on a 128x128 crop for 8 steps, extrapolated per 720p frame
-    onet = oracle.EvsNet(net_d["kind"], net_d["n_layers"], net_d["C"], net_d["kt"], net_d["ks"],
-                         net_d["beta"], net_d["vth"], net_d["reset"],
-                         np.asarray(net_d["w"], float), np.asarray(net_d["b"], float))
+    onet = oracle.EvsNet.from_dict(net_d)
     lf = inputs.random_logl_clip(0, 9, 128, 128)
     st = oracle.EvsState.new(onet, 128, 128)
     t0 = time.perf_counter()
@@ -156,11 +158,20 @@ def cpu_baseline(scene, net_d, spp, rows, frames_for_render=1):
     }
 
 
+def macs_per_pixel_step(d):
+    """Multiply-adds of one pixel-step: every conv layer (a stem layer 0 is one
+    step by ks0 x ks0) plus the projection."""
+    C, Lr, kt, ks, ks0 = d["C"], d["n_layers"], d["kt"], d["ks"], int(d.get("ks0", 0))
+    first = C * ks0 * ks0 if ks0 > 0 else C * kt * ks * ks
+    return first + (Lr - 1) * C * C * kt * ks * ks + C
+
+
 def net_desc(d):
     """Short description of an EvSNet's form (both arms print the same one)."""
     if d["kt"] > 1:
-        return "EvSNet temporal kernel %d, %d residual blocks, C%d + BiLIF" % (
-            d["kt"], (d["n_layers"] - 1) // 2, d["C"])
+        stem = ("%dx%d spatial stem, " % (d["ks0"], d["ks0"])) if int(d.get("ks0", 0)) > 0 else ""
+        return "EvSNet %stemporal kernel %d, %d residual blocks, C%d, delay %d + BiLIF" % (
+            stem, d["kt"], (d["n_layers"] - 1) // 2, d["C"], int(d.get("delay", 0)))
     return "EvSNet %d x conv%dx%d C%d + BiLIF" % (d["n_layers"], d["ks"], d["ks"], d["C"])
 
 
@@ -183,9 +194,7 @@ def run_reference(args):
     scene = inputs.city_block(seed=21)
     o = oracle.Scene(scene["tris"], scene["tri_mat"], scene["materials"], scene["lights"], scene["env"])
     _, net_d = load_net_host()
-    onet = oracle.EvsNet(net_d["kind"], net_d["n_layers"], net_d["C"], net_d["kt"], net_d["ks"],
-                         net_d["beta"], net_d["vth"], net_d["reset"],
-                         np.asarray(net_d["w"], float), np.asarray(net_d["b"], float))
+    onet = oracle.EvsNet.from_dict(net_d)
     rows_per_step = 4
     times, walls = [], []
     for s in range(args.warmup + args.steps):
@@ -229,13 +238,17 @@ def precision_sweep(api, _lib, net_d, logl, stream, reps=5):
     no spatial or temporal tolerance)."""
     import torch
     F, H, W = logl.shape
-    C, Lr = net_d["C"], net_d["n_layers"]
-    flops = 2.0 * (9 * C + (Lr - 1) * 9 * C * C + C) * H * W * (F - 1)
+    flops = 2.0 * macs_per_pixel_step(net_d) * H * W * (F - 1)
     out, ev_ref = {}, None
     for name, dt in (("f32", _lib.ET_F32), ("bf16", _lib.ET_BF16), ("fp8", _lib.ET_FP8)):
         net = api.EvsNetDev.from_dict(net_d, dt)
         buf = api.EventBuffer(F * H * W)
         ts = []
+        try:
+            api.evsnet_forward(logl[:2].contiguous(), net, api.EvsStateDev(net, H, W), t0=0, buf=buf)
+        except _lib.ETError as e:
+            out[name] = {"unsupported": str(e)}
+            continue
         for r in range(reps + 1):
             st = api.EvsStateDev(net, H, W)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -370,8 +383,7 @@ def run_rows(args):
         macs = kt * ks * ks * C_ + (Ln - 1) * kt * ks * ks * C_ * C_ + C_
         # forward, its recompute in the backward, data and weight gradients
         flops = 4 * 2.0 * macs * B * K * S * S
-        onet = oracle.EvsNet(d["kind"], Ln, C_, kt, ks, d["beta"], d["vth"], d["reset"],
-                             np.asarray(d["w"], float), np.asarray(d["b"], float))
+        onet = oracle.EvsNet.from_dict(d)
         xs = np.diff(np.asarray(clips[:1, :17, :32, :32].cpu().numpy(), np.float64), axis=1)
         es = E[:1, :16, :32, :32].cpu().numpy().astype(np.float64)
         tc = ctime(lambda: oracle.torch_grads(xs, es, onet))
@@ -399,8 +411,7 @@ def run_rows(args):
         C_, Ln, kt, ks = d["C"], d["n_layers"], d["kt"], d["ks"]
         macs = kt * ks * ks * C_ + (Ln - 1) * kt * ks * ks * C_ * C_ + C_
         flops = 2.0 * macs * npix * 10
-        onet = oracle.EvsNet(d["kind"], Ln, C_, kt, ks, d["beta"], d["vth"], d["reset"],
-                             np.asarray(d["w"], float), np.asarray(d["b"], float))
+        onet = oracle.EvsNet.from_dict(d)
         tc = ctime(lambda: oracle.evsnet_forward(lf_host[:, :64, :64], onet,
                                                  oracle.EvsState.new(onet, 64, 64), nthreads=cores))
         rows[name] = {"ms_per_frame": t * 1e3 / 10,
@@ -410,6 +421,137 @@ def run_rows(args):
                                        "kind": "oracle", "sample": "64 x 64 crop, 3 steps"}}
     print(json.dumps({"mode": "rows", "gpu": props.name, "fp32_peak_tflops": fp32,
                       "hbm_peak_gbs": hbm, "rows": rows}))
+
+
+def l2_copy_gbs(dev, mb=24, reps=50):
+    """Device copy bandwidth between two buffers that fit in L2 together (read +
+    write bytes over time), best of three rounds: the L2 roof of the traversal."""
+    import torch
+    n = mb * (1 << 20) // 4
+    a = torch.ones(n, dtype=torch.float32, device=dev)
+    b = torch.empty_like(a)
+    best = 0.0
+    for _ in range(3):
+        b.copy_(a)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            b.copy_(a)
+        e1.record()
+        torch.cuda.synchronize()
+        best = max(best, 2.0 * 4 * n * reps / (e0.elapsed_time(e1) / 1e3) / 1e9)
+    return best
+
+
+def _win(ev, lo, hi):
+    return ev[(ev[:, 2] >= lo) & (ev[:, 2] < hi)]
+
+
+def _f1s(api, pred, ref):
+    return [api.event_f1(pred, ref, d) for d in (0, 1, 2)]
+
+
+def _thr(api, frames, t0, dev):
+    import torch
+    F, H, W = frames.shape
+    ref = torch.zeros(H * W, dtype=torch.float64, device=dev)
+    return api.threshold_events(frames, C_THR, ref, False, t0=t0).host()
+
+
+def event_gate(api, inputs, g, net, dev, stream, s0, nb, spp, W, H, warm=64, n_1024=26, n_thr=26):
+    """Event F1 (delta = 0, 1, 2 frames; matching per pixel and polarity) of the
+    method -- EvSNet on `spp` frames, its state carried in from the `warm`
+    frames before -- against 256-SPP + threshold on the nb frames from s0; next
+    to the method without EvSNet (threshold on the same low-SPP frames), an
+    input-independent train at the reference's rate, and the reference's own
+    noise ceiling (a second 256-SPP seed; a 1024-SPP render).  Labels scored:
+    [s0 + 1, s0 + nb - delay), the steps the method has labelled by the last
+    frame.  Returns the dict of the bench line (plus the baseline's rate)."""
+    import torch
+    from paper_2508_18071_gb300 import train_evsnet
+    bpath = inputs.city_path(nb, first=s0)
+    lb = torch.empty((nb, H, W), dtype=torch.float32, device=dev)
+    ref = torch.zeros(H * W, dtype=torch.float64, device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    api.render_frames(g, bpath, W, H, 256, DEPTH, SEED, first_frame=s0, logl=lb, want_rgb=False)
+    bbuf = api.threshold_events(lb, C_THR, ref, False, t0=s0)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_b = e0.elapsed_time(e1) / 1e3
+    lo, hi = s0 + 1, s0 + nb - net.delay
+    ref_ev = _win(bbuf.host(), lo, hi)
+    out = {"_baseline_value": (nb / 1000.0) / (t_b / 60.0), "delta_frames": [0, 1, 2],
+           "frames": nb, "scored_labels": [lo, hi], "warm_frames": warm, "delay": net.delay}
+    # the method, state warmed on the frames before s0 (a video in progress)
+    lw = torch.empty((warm, H, W), dtype=torch.float32, device=dev)
+    api.render_frames(g, inputs.city_path(warm, first=s0 - warm), W, H, spp, DEPTH, SEED,
+                      first_frame=s0 - warm, logl=lw, want_rgb=False)
+    st = api.EvsStateDev(net, H, W)
+    api.evsnet_forward(lw, net, st, t0=s0 - warm)
+    del lw
+    lm = torch.empty((nb, H, W), dtype=torch.float32, device=dev)
+    api.render_frames(g, bpath, W, H, spp, DEPTH, SEED, first_frame=s0, logl=lm, want_rgb=False)
+    m_ev = _win(api.evsnet_forward(lm, net, st, t0=s0)[0].host(), lo, hi)
+    out["method"] = _f1s(api, m_ev, ref_ev)
+    out["n_ref"], out["n_method"] = len(ref_ev), len(m_ev)
+    fr = train_evsnet.fixed_rate_events(ref_ev, hi - lo, H, W, lo)
+    out["fixed_rate_control"] = _f1s(api, fr, ref_ev)
+    # threshold on the same low-SPP frames: ~3 events per pixel-step, so the
+    # first n_thr frames only
+    t_ev = _thr(api, lm[:n_thr].contiguous(), s0, dev)
+    r_short = _win(ref_ev, lo, s0 + n_thr)
+    out["threshold_on_low_spp"] = _f1s(api, t_ev, r_short)
+    out["threshold_on_low_spp_frames"] = n_thr
+    out["n_threshold_low_spp_per_step"] = len(t_ev) / (n_thr - 1)
+    out["method_same_frames_as_threshold"] = _f1s(api, _win(m_ev, lo, s0 + n_thr), r_short)
+    # noise ceiling of the reference
+    api.render_frames(g, bpath, W, H, 256, DEPTH, SEED + 1, first_frame=s0, logl=lb, want_rgb=False)
+    out["ceiling_second_256spp_render"] = _f1s(api, _win(_thr(api, lb, s0, dev), lo, hi), ref_ev)
+    del lb
+    lq = torch.empty((n_1024, H, W), dtype=torch.float32, device=dev)
+    api.render_frames(g, bpath[:n_1024], W, H, 1024, DEPTH, SEED + 2, first_frame=s0, logl=lq,
+                      want_rgb=False)
+    out["ceiling_1024spp_render"] = _f1s(api, _win(_thr(api, lq, s0, dev), lo, s0 + n_1024), r_short
+                                         if n_1024 == n_thr else _win(ref_ev, lo, s0 + n_1024))
+    out["ceiling_1024spp_frames"] = n_1024
+    out["gate_0.9_met"] = out["method"][1] >= 0.9
+    return out
+
+
+def event_gate_c2(api, inputs, dev, stream, nb=101, warm=64, spp=4, W=256, H=256):
+    """The same event scores on the 20k-triangle procedural scene of the
+    rotating-camera configuration (256 x 256, 4 SPP, depth 5), with the network
+    trained on that scene family."""
+    from paper_2508_18071_gb300 import train_evsnet
+    path = os.path.join(ROOT, "paper_2508_18071_gb300", "weights", "evsnet_random.npz")
+    if not os.path.exists(path):
+        return None
+    d = train_evsnet.load(path)
+    net = api.EvsNetDev.from_dict(d)
+    g = api.Scene(inputs.random_scene(seed=11))
+    s0 = warm
+    cams = inputs.random_scene_path(warm + nb)
+    lw = api.render_frames(g, cams[:warm], W, H, spp, DEPTH, 0, first_frame=0, want_rgb=False)[1]
+    lm = api.render_frames(g, cams[warm:], W, H, spp, DEPTH, 0, first_frame=s0, want_rgb=False)[1]
+    hi1 = api.render_frames(g, cams[warm:], W, H, 256, DEPTH, 7, first_frame=s0, want_rgb=False)[1]
+    hi2 = api.render_frames(g, cams[warm:], W, H, 256, DEPTH, 8, first_frame=s0, want_rgb=False)[1]
+    hq = api.render_frames(g, cams[warm:], W, H, 1024, DEPTH, 9, first_frame=s0, want_rgb=False)[1]
+    st = api.EvsStateDev(net, H, W)
+    api.evsnet_forward(lw, net, st, t0=0)
+    lo, hi = s0 + 1, s0 + nb - net.delay
+    ref_ev = _win(_thr(api, hi1, s0, dev), lo, hi)
+    m_ev = _win(api.evsnet_forward(lm, net, st, t0=s0)[0].host(), lo, hi)
+    return {"workload": "procedural scene %d tris, %dx%d, yaw 90 deg/s at 1 kHz, %d spp, depth %d, %s"
+                        % (len(inputs.random_scene(seed=11)["tris"]) + 4, W, H, spp, DEPTH, net_desc(d)),
+            "frames": nb, "scored_labels": [lo, hi], "delta_frames": [0, 1, 2],
+            "method": _f1s(api, m_ev, ref_ev),
+            "threshold_on_low_spp": _f1s(api, _win(_thr(api, lm, s0, dev), lo, hi), ref_ev),
+            "fixed_rate_control": _f1s(api, train_evsnet.fixed_rate_events(ref_ev, hi - lo, H, W, lo),
+                                       ref_ev),
+            "ceiling_second_256spp_render": _f1s(api, _win(_thr(api, hi2, s0, dev), lo, hi), ref_ev),
+            "ceiling_1024spp_render": _f1s(api, _win(_thr(api, hq, s0, dev), lo, hi), ref_ev),
+            "n_ref": len(ref_ev), "n_method": len(m_ev)}
 
 
 def load_net_host():
@@ -451,15 +593,36 @@ def main():
     g = api.Scene(scene, builder=args.bvh)
     info = g.info()
     info["build_s"] = time.perf_counter() - tb0
+    if args.evsnet_dtype == "auto":
+        # BF16 where the library has a tensor-core kernel for the network's form
+        _, d_probe = load_net_host()
+        probe = api.EvsNetDev.from_dict(d_probe, _lib.ET_BF16)
+        try:
+            api.evsnet_forward(torch.zeros((2, 8, 8), device=dev), probe, api.EvsStateDev(probe, 8, 8))
+            args.evsnet_dtype = "bf16"
+        except _lib.ETError:
+            args.evsnet_dtype = "f32"
     dtype = {"f32": _lib.ET_F32, "bf16": _lib.ET_BF16, "fp8": _lib.ET_FP8}[args.evsnet_dtype]
     net, net_d = load_net(dtype)
     F = args.frames
-    npix = W_ * H_
-    # weak scaling: every rank renders its own segment of the camera path
-    first = 1000 * rank
+    # the partition across ranks: row bands (each rank renders its rows of every
+    # frame plus the halo its EvSNet reads, and keeps its own rows' events; the
+    # job processes whole frames) or frame segments (every rank its own segment
+    # of the camera path)
+    from paper_2508_18071_gb300 import sharding
+    halo = (int(net_d.get("ks0", 0)) // 2 if int(net_d.get("ks0", 0)) > 0 else
+            (net.n_layers * (net.ks // 2) if net.ks > 1 else 0))
+    if args.shard == "bands":
+        y0, y1, h0, h1 = sharding.row_bands(H_, world, halo=halo)[rank]
+        first = 0
+    else:
+        y0, y1, h0, h1 = 0, H_, 0, H_
+        first = 1000 * rank
+    Hb = h1 - h0
+    npix = W_ * Hb
     path = inputs.city_path(F * (args.warmup + args.steps) + 1, first=first)
-    logl = torch.empty((F, H_, W_), dtype=torch.float32, device=dev)
-    state = api.EvsStateDev(net, H_, W_)
+    logl = torch.empty((F, Hb, W_), dtype=torch.float32, device=dev)
+    state = api.EvsStateDev(net, Hb, W_)
     buf = api.EventBuffer(F * npix)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
@@ -470,7 +633,7 @@ def main():
         if ev_r is not None:
             ev_r[0].record(stream)
         api.render_frames(g, cams, W_, H_, args.spp, DEPTH, SEED, first_frame=f0, logl=logl,
-                          want_rgb=False)
+                          want_rgb=False, rows=(h0, h1))
         if ev_r is not None:
             ev_r[1].record(stream)
         api.evsnet_forward(logl, net, state, t0=f0, buf=buf)
@@ -511,20 +674,22 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
     n_ev_last = buf.n()
-    video_s = world * args.steps * F / 1000.0
+    # video seconds the whole job processed: bands split every frame, segments
+    # add up
+    video_s = (1 if args.shard == "bands" else world) * args.steps * F / 1000.0
     value = video_s / (total_ms / 1000.0 / 60.0)
 
     # ---- end to end through the public API: host cameras in, events to host out
     pinned = torch.empty((F * npix, 3), dtype=torch.int32, pin_memory=True)
     cnt_host = torch.empty(1, dtype=torch.int64, pin_memory=True)
     e2e_t, d2h = [], []
-    state_e = api.EvsStateDev(net, H_, W_)
+    state_e = api.EvsStateDev(net, Hb, W_)
     for k in range(args.warmup + args.steps):
         f0 = first + k * F
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         api.render_frames(g, path[k * F:(k + 1) * F], W_, H_, args.spp, DEPTH, SEED,
-                          first_frame=f0, logl=logl, want_rgb=False)
+                          first_frame=f0, logl=logl, want_rgb=False, rows=(h0, h1))
         api.evsnet_forward(logl, net, state_e, t0=f0, buf=buf)
         cnt_host.copy_(buf.count, non_blocking=True)
         torch.cuda.synchronize()
@@ -534,12 +699,16 @@ def main():
         if k >= args.warmup:
             e2e_t.append(time.perf_counter() - t0)
             d2h.append(12 * n + 8)
-    e2e_value = world * args.steps * F / 1000.0 / (sum(e2e_t) / 60.0)
+    e2e_value = video_s / (sum(e2e_t) / 60.0)
+    if world > 1:
+        t = torch.tensor([sum(e2e_t)], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_value = video_s / (float(t.item()) / 60.0)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
+        "scaling": "strong" if (args.shard == "bands" and world > 1) else "weak", "vs_baseline": None,
         "dtype": "f32 render + %s EvSNet" % args.evsnet_dtype,
         "data": "synthetic (procedural city block, random-init EvSNet)" if not net_d.get("trained")
                 else "synthetic (procedural city block, EvSNet trained on procedural clips)",
@@ -547,7 +716,10 @@ def main():
                    "frames_per_step": F, "l2": "flushed between steps (256 MB write)",
                    "bvh": {"builder": info["builder"], "nodes": info["n_nodes"],
                            "sah_cost": info["sah_cost"], "build_s": info["build_s"]},
-                   "parallelism": "replicas: each rank renders its own path segment"},
+                   "parallelism": ("row bands: rank r renders rows [y0, y1) of every frame plus "
+                                   "%d halo rows (no data-path collective)" % halo)
+                                  if args.shard == "bands" else
+                                  "frame segments: each rank renders its own path segment"},
         "wall_s_timed": wall,
         "gpu_launches": launches,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 52 * F,
@@ -561,8 +733,7 @@ def main():
         "clocks": clk.summary(local),
     }
     # EvSNet kernel: algorithmic MACs per pixel-step of the conv stack + projection
-    C, Lr = net.C, net.n_layers
-    macs = 9 * C + (Lr - 1) * 9 * C * C + C
+    macs = macs_per_pixel_step(net_d)
     flops_evs = 2.0 * macs * npix * F
     t_evs_s = statistics.mean(t_evs) / 1e3
     peaks = {}
@@ -577,12 +748,16 @@ def main():
             # nominal dense fp8 / bf16 ratio (4.5 / 2.25 PFLOP/s)
             pk *= 2.0
             src += " x 2 (nominal fp8 / bf16 ratio)"
-        line["roofline_evsnet"] = {"bound": "tensor", "kernel": "evsnet_tc_kernel",
-                                   "achieved": flops_evs / t_evs_s / 1e12, "peak": pk,
-                                   "unit": "TFLOP/s", "frac": flops_evs / t_evs_s / 1e12 / pk,
-                                   "traffic": None, "peak_source": src,
-                                   "work": "%d MAC per pixel-step (4 x conv3x3 C%d + projection)"
-                                           % (macs, C)}
+        bound, kname = "tensor", "evsnet tensor-core kernel"
+    else:
+        pk = props.multi_processor_count * FP32_LANES_PER_SM * 2 * 2.07e9 / 1e12
+        src = "derived, not measured: SMs x 128 FP32 lanes x 2 x 2.07 GHz"
+        bound, kname = "alu", "evsnet FP32 kernel"
+    line["roofline_evsnet"] = {"bound": bound, "kernel": kname,
+                               "achieved": flops_evs / t_evs_s / 1e12, "peak": pk,
+                               "unit": "TFLOP/s", "frac": flops_evs / t_evs_s / 1e12 / pk,
+                               "traffic": None, "peak_source": src,
+                               "work": "%d MAC per pixel-step (%s)" % (macs, net_desc(net_d))}
     if not args.no_sweep:
         line["evsnet_precision_sweep"] = precision_sweep(api, _lib, net_d, logl, stream)
     if rank != 0:
@@ -596,83 +771,80 @@ def main():
         line["cpu_baseline"] = cpu
         flops_launch = work["flops_per_ray"] * work["rays_per_sample"] * npix * args.spp * F
         line["mrays_per_s"] = work["rays_per_sample"] * npix * args.spp * F / (statistics.mean(t_render) / 1e3) / 1e6
-        # the second traversal bound: algorithmic node + triangle bytes
-        # per ray against HBM (above 1: the hierarchy is served from L1 / L2)
-        bytes_launch = work["bytes_per_ray"] * work["rays_per_sample"] * npix * args.spp * F
+        # per-kernel times and queue lengths of one step's render (events around
+        # every launch, outside the timed region)
+        g.profile(True)
+        api.render_frames(g, path[:F], W_, H_, args.spp, DEPTH, SEED, first_frame=first,
+                          want_rgb=False)
+        prof = g.profile_read()
+        g.profile(False)
         hbm = peaks.get("hbm_gbs") or 6800.0
-        line["roofline_traversal_bytes"] = {
-            "bound": "hbm", "achieved": bytes_launch / (statistics.mean(t_render) / 1e3) / 1e9,
-            "peak": hbm, "unit": "GB/s",
-            "frac": bytes_launch / (statistics.mean(t_render) / 1e3) / 1e9 / hbm,
-            "work": "64 B per node visit + 36 B per triangle test (%.0f B/ray)" % work["bytes_per_ray"],
-            "peak_source": "MEASURED_PEAKS hbm_gbs (of measured)" if "hbm_gbs" in peaks
-                           else "fallback 6.8 TB/s",
-            "note": "algorithmic bytes; the measured DRAM traffic of wf_trace is ~1 % of its "
-                    "peak (profiles/wf_trace_v3_city320x180.md): L1 / L2 serve them"}
+        hbm_src = "MEASURED_PEAKS hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback 6.8 TB/s"
+        l2 = l2_copy_gbs(dev)
+        fp32_peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * 2.07e9 / 1e12
+        fp32_src = ("derived, not measured: %d SMs x 128 FP32 lanes x 2 x 2.07 GHz (unit counts and "
+                    "maximum clock; the measured peaks hold no FP32 figure)" % props.multi_processor_count)
+        t_tr = (prof["trace"][0] + prof["shadow"][0]) / 1e3
+        rays = prof["trace"][2] + prof["shadow"][2] if prof["trace"][2] is not None else None
+        kern = {}
+        if rays:
+            kern["wf_trace"] = {
+                "launches": prof["trace"][1] + prof["shadow"][1], "ms": t_tr * 1e3, "rays": rays,
+                "share_of_render": t_tr * 1e3 / sum(v[0] for v in prof.values()),
+                "alu": {"bound": "alu", "achieved": work["flops_per_ray"] * rays / t_tr / 1e12,
+                        "peak": fp32_peak, "unit": "TFLOP/s",
+                        "frac": work["flops_per_ray"] * rays / t_tr / 1e12 / fp32_peak,
+                        "peak_source": fp32_src},
+                "l2": {"bound": "l2", "achieved": work["bytes_per_ray"] * rays / t_tr / 1e9, "peak": l2,
+                       "unit": "GB/s", "frac": work["bytes_per_ray"] * rays / t_tr / 1e9 / l2,
+                       "peak_source": "measured here: device copy of 24 MB within L2 (read + write)",
+                       "work": "64 B per node visit + 36 B per triangle test (%.0f B/ray, full-sweep "
+                               "SAH counts)" % work["bytes_per_ray"]}}
+            # bytes each kernel reads and writes per item, from the queue records
+            # (wavefront state: rays 32 B, path state 16 + 16 B, hits 8 B, shadow
+            # rays 48 B, triangles 48 B)
+            per_item = {"raygen": (64.0, "paths", "64 B written per path (ray 32 B, throughput 16 B, "
+                                   "radiance 16 B)"),
+                        "shade": (232.0, "hits", "<= 232 B per shaded hit: hit 8 + ray 32 + path state "
+                                  "32 + triangle 48 read, path state 32 + next ray 32 + shadow ray 48 "
+                                  "written"),
+                        "accumulate": (16.0 * args.spp + 4.0, "pixel-frames",
+                                       "%d B per pixel-frame: %d path radiances of 16 B read, log "
+                                       "luminance 4 B written" % (16 * args.spp + 4, args.spp))}
+            for k, (b, unit, note) in per_item.items():
+                ms, n, items = prof[k]
+                kern["wf_" + k] = {"launches": n, "ms": ms, unit: items,
+                                   "share_of_render": ms / sum(v[0] for v in prof.values()),
+                                   "hbm": {"bound": "hbm", "achieved": b * items / (ms / 1e3) / 1e9,
+                                           "peak": hbm, "unit": "GB/s",
+                                           "frac": b * items / (ms / 1e3) / 1e9 / hbm,
+                                           "peak_source": hbm_src, "work": note}}
+        line["render_kernels"] = kern
+        line["render_profile_note"] = ("one step's %d frames rendered again with an event around each "
+                                       "launch (et_render_profile), after the timed region" % F)
         t_launch = statistics.mean(t_render) / 1e3
-        peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * 2.07e9 / 1e12
         line["roofline"] = {"bound": "alu", "achieved": flops_launch / t_launch / 1e12,
-                            "peak": peak, "unit": "TFLOP/s",
-                            "frac": flops_launch / t_launch / 1e12 / peak, "traffic": None,
+                            "peak": fp32_peak, "unit": "TFLOP/s",
+                            "frac": flops_launch / t_launch / 1e12 / fp32_peak, "traffic": None,
                             "kernel": "wavefront render (wf_trace closest/shadow, wf_shade, "
-                                      "wf_raygen, wf_accumulate); wf_trace ~81 % of it",
+                                      "wf_raygen, wf_accumulate); per-kernel rows in render_kernels",
                             "work": "24 flop per BVH node visit + 40 per triangle test, counted by "
                                     "the oracle's full-sweep SAH BVH on the sampled rays (%.1f "
                                     "rays/sample, %.0f flop/ray)" % (work["rays_per_sample"],
                                                                      work["flops_per_ray"]),
-                            "peak_source": "%d SMs x 128 FP32 lanes x 2 x 2.07 GHz (recipe unit "
-                                           "counts and max clock)" % props.multi_processor_count}
+                            "peak_source": fp32_src}
 
     # ---- the metric's baseline: 256 spp + contrast threshold, same kernels
     if not args.no_baseline:
-        nb = args.baseline_frames
-        bpath = inputs.city_path(nb, first=first + 10000)
-        lb = torch.empty((nb, H_, W_), dtype=torch.float32, device=dev)
-        ref = torch.zeros(npix, dtype=torch.float64, device=dev)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        api.render_frames(g, bpath, W_, H_, 256, DEPTH, SEED, first_frame=first + 10000, logl=lb,
-                          want_rgb=False)
-        bbuf = api.threshold_events(lb, C_THR, ref, False, t0=first + 10000)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        t_b = e0.elapsed_time(e1) / 1e3
-        base_value = (nb / 1000.0) / (t_b / 60.0)
-        ref_ev = bbuf.host()
-        # the reference's own noise floor: a second, independently seeded 256-SPP render
-        api.render_frames(g, bpath, W_, H_, 256, DEPTH, SEED + 1, first_frame=first + 10000, logl=lb,
-                          want_rgb=False)
-        ref_b = torch.zeros(npix, dtype=torch.float64, device=dev)
-        ref2_ev = api.threshold_events(lb, C_THR, ref_b, False, t0=first + 10000).host()
-        # the method on the same frames (fresh state) and the method without EvSNet
-        lm = torch.empty((nb, H_, W_), dtype=torch.float32, device=dev)
-        api.render_frames(g, bpath, W_, H_, args.spp, DEPTH, SEED, first_frame=first + 10000,
-                          logl=lm, want_rgb=False)
-        st2 = api.EvsStateDev(net, H_, W_)
-        m_ev = api.evsnet_forward(lm, net, st2, t0=first + 10000)[0].host()
-        # the same frames with the EvSNet state carried in from the WARM frames of
-        # the path before them (a video in progress rather than a fresh start)
-        WARM = 64
-        lw = torch.empty((WARM, H_, W_), dtype=torch.float32, device=dev)
-        api.render_frames(g, inputs.city_path(WARM, first=first + 10000 - WARM), W_, H_, args.spp,
-                          DEPTH, SEED, first_frame=first + 10000 - WARM, logl=lw, want_rgb=False)
-        st3 = api.EvsStateDev(net, H_, W_)
-        api.evsnet_forward(lw, net, st3, t0=first + 10000 - WARM)
-        mw_ev = api.evsnet_forward(lm, net, st3, t0=first + 10000)[0].host()
-        del lw
-        ref2 = torch.zeros(npix, dtype=torch.float64, device=dev)
-        t_ev = api.threshold_events(lm, C_THR, ref2, False, t0=first + 10000).host()
+        gate = event_gate(api, inputs, g, net, dev, stream, first + 10000, args.baseline_frames, args.spp,
+                          W_, H_)
+        base_value = gate.pop("_baseline_value")
         line["baseline_256spp_threshold"] = {
-            "value": base_value, "unit": UNIT, "frames_measured": nb,
+            "value": base_value, "unit": UNIT, "frames_measured": args.baseline_frames,
             "speedup_of_method": value / base_value}
-        line["event_f1_vs_baseline"] = {
-            "delta_frames": 1, "frames": nb - 1, "method": api.event_f1(m_ev, ref_ev, 1),
-            "method_state_warmed": api.event_f1(mw_ev, ref_ev, 1), "warm_frames": WARM,
-            "n_method_state_warmed": len(mw_ev),
-            "threshold_on_low_spp": api.event_f1(t_ev, ref_ev, 1),
-            "ceiling_second_256spp_render": api.event_f1(ref2_ev, ref_ev, 1),
-            "n_ref": len(ref_ev), "n_method": len(m_ev), "n_threshold_low_spp": len(t_ev),
-            "gate_0.9_met": api.event_f1(m_ev, ref_ev, 1) >= 0.9}
+        line["event_f1_vs_baseline"] = gate
+        if not args.no_c2:
+            line["event_f1_c2"] = event_gate_c2(api, inputs, dev, stream)
     print(json.dumps(line))
 
 

@@ -141,6 +141,16 @@ int et_render_frames(const et_scene* scene, const et_camera* cams, int32_t n_fra
                      int32_t max_depth, uint64_t seed, float* rgb, float* logl,
                      int32_t log_mode, float log_param, int32_t* records, void* stream);
 
+/* Rows y0 <= y < y1 of the same W x H frames (0 <= y0 < y1 <= H): rgb, logl and
+ * records are [n_frames][y1 - y0][W]..., bit for bit those rows of the full
+ * frames (rays and random numbers keep the full image's pixel index).  This is
+ * the unit of the row-band partition across GPUs.  Errors as et_render_frames,
+ * and ET_ERR_ARG for an empty or out-of-range band. */
+int et_render_rows(const et_scene* scene, const et_camera* cams, int32_t n_frames,
+                   int32_t first_frame, int32_t W, int32_t H, int32_t y0, int32_t y1, int32_t spp,
+                   int32_t max_depth, uint64_t seed, float* rgb, float* logl, int32_t log_mode,
+                   float log_param, int32_t* records, void* stream);
+
 /* Annotations of the primary hit through each pixel centre (no jitter), the
  * by-products that come with the rendered events (the paper's outputs extend
  * to depth and segmentation, Sec. 1), for n_frames cameras:
@@ -172,6 +182,21 @@ int et_render_annotations(const et_scene* scene, const et_camera* cams, int32_t 
  * Errors: ET_ERR_ARG. */
 enum { ET_RENDER_WAVEFRONT = 0, ET_RENDER_MEGAKERNEL = 1 };
 int et_render_set_mode(et_scene* scene, int32_t mode);
+
+/* Per-kernel device time of the wavefront schedule, for measurement (not part
+ * of the method).  et_render_profile(scene, 1): every later et_render_frames
+ * call on this scene records a CUDA event before and after each of its
+ * kernels and copies the length of the queue each kernel processed to pinned
+ * host memory (allocated here, once); 0 stops recording.  Events add a little
+ * time of their own; leave profiling off for timed runs of the whole call.
+ * et_render_profile_read waits for the recorded work and returns, summed since
+ * the previous read and indexed raygen 0, closest-hit trace 1, shade 2,
+ * shadow trace 3, accumulate 4: ms[5] device milliseconds, launches[5], and
+ * items[5] = paths generated, rays traced, hits shaded, shadow rays traced and
+ * pixel-frames resolved.  ET_ERR_CAPACITY: more than 32768 queue lengths were
+ * recorded between reads (the times stay valid, the counts are short). */
+int et_render_profile(et_scene* scene, int32_t enable);
+int et_render_profile_read(et_scene* scene, double* ms, int64_t* launches, int64_t* items);
 
 /* ---------------------------------------------------------- threshold events
  * Sec. 3.1 contrast-threshold model (the method without EvSNet, the 256-SPP
@@ -250,11 +275,22 @@ int et_sensor_events(const float* logl, int32_t F, int32_t H, int32_t W,
  *   layer inputs per layer, 32x16 pixel tile and step, each by the power of two
  *   that brings its absolute maximum to at most 448 (exact to undo).
  *   Layer 0, the projection and BiLIF stay FP32 in both.
+ * ks0 (this library's spatio-temporal form; the paper's EvSNet is pixel-wise):
+ *   0, or an odd size 1..7 that makes layer 0 a one-step ks0 x ks0 spatial
+ *   convolution of the current X (weights W[C][1][1][ks0][ks0], zero padding)
+ *   ahead of temporal layers (ks = 1); layer 0 then keeps no history.  The
+ *   CUDA kernels take ks0 > 0 only with ks = 1.
+ * delay >= 0: the events of step k carry t = t0 + k - delay (a network trained
+ *   on a window centred delay steps back labels its output with that centre;
+ *   the Sec. 4.1 network with "same" padding corresponds to delay 21); steps
+ *   whose label would be negative emit no events.
  */
 typedef struct {
   int32_t kind, n_layers, C, kt, ks;
   float beta, vth, reset;
   int32_t dtype;
+  int32_t ks0;        /* 0: layer 0 is kt x ks x ks; > 0: one step, ks0 x ks0 */
+  int32_t delay;      /* event label offset (steps) */
   const float* w;     /* device */
   const float* b;     /* device */
 } et_evsnet_weights;

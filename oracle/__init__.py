@@ -519,8 +519,11 @@ def _heaviside_fn():
     return Heaviside
 
 
-def torch_forward(X, net: EvsNet, params=None, smooth=False, alpha=2.0, V0=None):
+def torch_forward(X, net: EvsNet, params=None, smooth=False, alpha=2.0, V0=None, round_bf16=False):
     """EvSNet on log differences X [B,K,H,W] (torch float64); returns (S_on, S_off, I, Vp).
+
+    round_bf16: the library's BF16 mode -- the weights of layers 1.. and their
+    input activations rounded to BF16 (round to nearest even), every sum exact.
 
     Spikes (Eq. 3, reading: fire on V'): S_on = Theta(V' - Vth), S_off =
     Theta(-V' - Vth), S = S_on - S_off, reset V = V' - r S (not detached).
@@ -539,15 +542,22 @@ def torch_forward(X, net: EvsNet, params=None, smooth=False, alpha=2.0, V0=None)
         h = F.pad(h, (pad, pad, pad, pad, kt - 1, 0))
         return F.conv3d(h, Wt, bt)
 
+    def rb(t):
+        return t.to(torch.bfloat16).to(t.dtype) if round_bf16 else t
+
+    def convr(h, Wt, bt):
+        # a tensor-core layer: BF16 operands in the library's BF16 mode
+        return conv(rb(h), rb(Wt), bt)
+
     x = X.unsqueeze(1)
     h = torch.relu(conv(x, *layers[0]))
     if net.kind == 0:
         for Wt, bt in layers[1:]:
-            h = torch.relu(conv(h, Wt, bt))
+            h = torch.relu(convr(h, Wt, bt))
     else:
         for j in range(1, net.n_layers - 1, 2):
-            a = torch.relu(conv(h, *layers[j]))
-            h = torch.relu(h + conv(a, *layers[j + 1]))
+            a = torch.relu(convr(h, *layers[j]))
+            h = torch.relu(h + convr(a, *layers[j + 1]))
     I = torch.einsum("bckhw,c->bkhw", h, wp) + bp[0]
     Hv = _heaviside_fn()
     V = torch.zeros(B, H, W, dtype=X.dtype) if V0 is None else V0

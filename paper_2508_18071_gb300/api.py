@@ -80,6 +80,23 @@ class Scene:
         """ET_RENDER_WAVEFRONT (default) or ET_RENDER_MEGAKERNEL."""
         L.check("et_render_set_mode", L.load().et_render_set_mode(self._h, int(mode)))
 
+    PROFILE_KINDS = ("raygen", "trace", "shade", "shadow", "accumulate")
+
+    def profile(self, enable: bool):
+        """et_render_profile: record per-kernel events in later renders."""
+        L.check("et_render_profile", L.load().et_render_profile(self._h, int(bool(enable))))
+
+    def profile_read(self) -> dict:
+        """et_render_profile_read: {kind: (ms, launches, items)} since the last read."""
+        ms = (C.c_double * 5)()
+        n = (C.c_int64 * 5)()
+        it = (C.c_int64 * 5)()
+        st = L.load().et_render_profile_read(self._h, ms, n, it)
+        if st not in (L.ET_OK, L.ET_ERR_CAPACITY):
+            L.check("et_render_profile_read", st)
+        return {k: (ms[i], n[i], it[i] if st == L.ET_OK else None)
+                for i, k in enumerate(self.PROFILE_KINDS)}
+
     def info(self):
         n, nn, sah = C.c_int64(), C.c_int64(), C.c_double()
         L.check("et_scene_info", L.load().et_scene_info(self._h, C.byref(n), C.byref(nn), C.byref(sah)))
@@ -108,20 +125,26 @@ def cameras(cams) -> C.Array:
 
 def render_frames(scene: Scene, cams, W, H, spp, max_depth, seed, first_frame=0, rgb=None,
                   logl=None, want_rgb=True, want_logl=True, log_mode=L.ET_LOG_EPS,
-                  log_param=1e-3, records=False, stream=None):
-    """et_render_frames; returns (rgb [F,H,W,3] or None, logl [F,H,W] or None, records or None)."""
+                  log_param=1e-3, records=False, stream=None, rows=None):
+    """et_render_frames (or et_render_rows for rows = (y0, y1)); returns
+    (rgb [F,h,W,3] or None, logl [F,h,W] or None, records or None), h = H or y1 - y0."""
     F = np.asarray(cams, np.float32).reshape(-1, 13).shape[0]
     cams_c = cameras(cams)
     dev = torch.device("cuda")
+    y0, y1 = (0, H) if rows is None else (int(rows[0]), int(rows[1]))
+    h = y1 - y0
     if want_rgb and rgb is None:
-        rgb = torch.empty((F, H, W, 3), dtype=torch.float32, device=dev)
+        rgb = torch.empty((F, h, W, 3), dtype=torch.float32, device=dev)
     if want_logl and logl is None:
-        logl = torch.empty((F, H, W), dtype=torch.float32, device=dev)
-    rec = torch.empty((F, H, W, spp, max_depth, 2), dtype=torch.int32, device=dev) if records else None
-    st = L.load().et_render_frames(scene._h, cams_c, F, first_frame, W, H, spp, max_depth,
-                                   C.c_uint64(seed), _ptr(rgb if want_rgb else None),
-                                   _ptr(logl if want_logl else None), log_mode, float(log_param),
-                                   _ptr(rec), _stream(stream))
+        logl = torch.empty((F, h, W), dtype=torch.float32, device=dev)
+    rec = torch.empty((F, h, W, spp, max_depth, 2), dtype=torch.int32, device=dev) if records else None
+    args = (C.c_uint64(seed), _ptr(rgb if want_rgb else None), _ptr(logl if want_logl else None),
+            log_mode, float(log_param), _ptr(rec), _stream(stream))
+    if rows is None:
+        st = L.load().et_render_frames(scene._h, cams_c, F, first_frame, W, H, spp, max_depth, *args)
+    else:
+        st = L.load().et_render_rows(scene._h, cams_c, F, first_frame, W, H, y0, y1, spp, max_depth,
+                                     *args)
     L.check("et_render_frames", st)
     return (rgb if want_rgb else None), (logl if want_logl else None), rec
 
@@ -319,18 +342,23 @@ class EvsNetDev:
     w: torch.Tensor
     b: torch.Tensor
     dtype: int = L.ET_F32
+    ks0: int = 0
+    delay: int = 0
 
     @staticmethod
     def from_dict(d: dict, dtype=L.ET_F32):
         return EvsNetDev(d["kind"], d["n_layers"], d["C"], d["kt"], d["ks"], float(d["beta"]),
                          float(d["vth"]), float(d["reset"]),
                          torch.as_tensor(np.asarray(d["w"], np.float32)).cuda().contiguous(),
-                         torch.as_tensor(np.asarray(d["b"], np.float32)).cuda().contiguous(), dtype)
+                         torch.as_tensor(np.asarray(d["b"], np.float32)).cuda().contiguous(), dtype,
+                         int(d.get("ks0", 0)), int(d.get("delay", 0)))
 
-    def c_struct(self):
+    def c_struct(self, w=None, b=None):
+        w = self.w if w is None else w
+        b = self.b if b is None else b
         return L.et_evsnet_weights(self.kind, self.n_layers, self.C, self.kt, self.ks, self.beta,
-                                   self.vth, self.reset, self.dtype, self.w.data_ptr(),
-                                   self.b.data_ptr())
+                                   self.vth, self.reset, self.dtype, self.ks0, self.delay,
+                                   w.data_ptr(), b.data_ptr())
 
 
 class EvsStateDev:

@@ -148,7 +148,7 @@ __global__ void evsnet_f32_kernel(Params P, const float* __restrict__ logl, cons
       const float vp = P.beta * V + I;
       S = vp >= P.vth ? 1 : (vp <= -P.vth ? -1 : 0);
       V = vp - P.reset * (float)S;
-      nev = S != 0 ? 1u : 0u;
+      nev = (S != 0 && P.t0 + f >= 0) ? 1u : 0u;   // delayed labels below 0: none
       if (I_out) I_out[(int64_t)step * npix + q] = I;
       if (spikes) spikes[(int64_t)step * npix + q] = (int8_t)S;
     }

@@ -236,7 +236,7 @@ evsnet_f32s_kernel(SParams P, int C, const float* __restrict__ logl, const float
             const float vp = P.beta * Vs[ti] + I;               // Eq. 2-3
             S = vp >= P.vth ? 1 : (vp <= -P.vth ? -1 : 0);
             Vs[ti] = vp - P.reset * (float)S;
-            nev = S != 0 ? 1u : 0u;
+            nev = (S != 0 && P.t0 + f >= 0) ? 1u : 0u;   // delayed labels below 0: none
             const int64_t o = (int64_t)(f - P.f0) * npix + (int64_t)gy * P.W + gx;
             if (I_out) I_out[o] = I;
             if (spikes) spikes[o] = (int8_t)S;

@@ -350,7 +350,7 @@ evsnet_tc_kernel(TcParams P, const float* __restrict__ logl, const float* __rest
               const float vp = P.beta * Vs[ti] + I;
               S = vp >= P.vth ? 1 : (vp <= -P.vth ? -1 : 0);
               Vs[ti] = vp - P.reset * (float)S;
-              nev = S != 0 ? 1u : 0u;
+              nev = (S != 0 && P.t0 + f >= 0) ? 1u : 0u;   // delayed labels below 0: none
               const int64_t q = (int64_t)(f - (P.f0 == 0 ? 0 : 1)) * npix + (int64_t)gy * P.W + gx;
               if (I_out) I_out[q] = I;
               if (spikes) spikes[q] = (int8_t)S;

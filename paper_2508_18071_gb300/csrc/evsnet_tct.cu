@@ -1,0 +1,334 @@
+// EvSNet forward on the tcgen05 tensor cores for the pixel-wise temporal form:
+// the paper's network (Sec. 4.1, Eq. 5: convolutions of kernel kt along time,
+// plain stack or residual blocks; Eq. 6 projection; BiLIF of Eq. 2-3), with or
+// without a one-step spatial stem as layer 0.  BF16 operands (the weights of
+// layers 1.. and their inputs), FP32 accumulation in TMEM; layer 0, the
+// residual sums, the projection and BiLIF stay FP32.
+//
+// A CTA owns a tile of 128 consecutive pixels for the whole call: one thread
+// per pixel, one TMEM lane per pixel.  The input history of every layer >= 1
+// (its last kt inputs) lives in shared memory as a ring of kt + kT - 1 slots,
+// each slot one step of 128 pixels x 16 channels in the K-major, no-swizzle
+// operand layout (two 2 KB planes of 8 channels, 16-byte rows), so the A
+// operand of tap tau is simply the slot of step s - (kt - 1) + tau: a layer's
+// output for kT consecutive steps is kT x kt MMAs of M = 128, N = 16, K = 16,
+// accumulated in kT groups of 16 TMEM columns.  One step of a layer therefore
+// costs one MMA round trip (issue, commit, mbarrier wait, tcgen05.ld) per kT
+// steps; the epilogue (bias, ReLU, residual add, BF16 rounding) writes the
+// next layer's ring slot, or, after the last layer, feeds the projection and
+// BiLIF.  The caller's FP32 history state ([layer][kt-1][C][H][W]) is read
+// into the rings at the start and written back at the end; values written
+// by this kernel are BF16-rounded, so a later call of the BF16 path reads them
+// back exactly.
+//
+// MMA waits are bounded; on expiry the kernel sets bit 62 of the event count,
+// leaves the membrane and history state untouched, waits (bounded) for its
+// MMAs in flight and frees its TMEM.
+#include "et_internal.cuh"
+#include "event_emit.cuh"
+#include "evsnet_common.h"
+#include "tc_ptx.cuh"
+#include <cuda_bf16.h>
+
+namespace {
+
+constexpr int TP = 128;                 // pixels per tile = MMA M = TMEM lanes
+constexpr int CP = 16;                  // channels (C <= 16, zero-padded)
+constexpr int kT = 2;                   // steps per MMA round trip
+constexpr int kMaxKt = 7;
+constexpr int kMaxStem = 7;
+constexpr int kSlot = TP * CP * 2;      // bytes of one ring slot
+constexpr int kPlane = TP * 16;         // bytes of 8 channels of 128 rows
+constexpr int kThreads = TP;
+constexpr uint32_t kTmemCols = 32;      // kT x 16 accumulator columns
+constexpr unsigned long long kTimeoutBit = 1ull << 62;
+
+struct TctParams {
+  int H, W, F, f0, t0;
+  int L, C, kt, ks0, kind;
+  float beta, vth, reset;
+  int R;                                // ring slots per layer: kt + kT - 1
+  int woff[kMaxLayers + 1];             // packed weight offsets per layer (+ projection)
+  int off_wB, off_f32;                  // shared-memory byte offsets
+  uint32_t wait_iters;
+};
+
+__device__ __forceinline__ int ring_pos(int s, int R) { return ((s % R) + R) % R; }
+
+// one pixel's 16 channels, BF16-rounded, as row `m` of a ring slot
+__device__ __forceinline__ void store_row(unsigned char* slot, int m, const float* v) {
+  __align__(16) __nv_bfloat162 h[CP / 2];
+#pragma unroll
+  for (int c = 0; c < CP / 2; ++c) h[c] = __floats2bfloat162_rn(v[2 * c], v[2 * c + 1]);
+  *reinterpret_cast<uint4*>(slot + m * 16) = reinterpret_cast<const uint4*>(h)[0];
+  *reinterpret_cast<uint4*>(slot + kPlane + m * 16) = reinterpret_cast<const uint4*>(h)[1];
+}
+
+__device__ __forceinline__ void load_row(const unsigned char* slot, int m, float* v) {
+  __align__(16) __nv_bfloat162 h[CP / 2];
+  reinterpret_cast<uint4*>(h)[0] = *reinterpret_cast<const uint4*>(slot + m * 16);
+  reinterpret_cast<uint4*>(h)[1] = *reinterpret_cast<const uint4*>(slot + kPlane + m * 16);
+#pragma unroll
+  for (int c = 0; c < CP / 2; ++c) {
+    const float2 f = __bfloat1622float2(h[c]);
+    v[2 * c] = f.x;
+    v[2 * c + 1] = f.y;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+evsnet_tct_kernel(TctParams P, const float* __restrict__ logl, const float* __restrict__ wg,
+                  const float* __restrict__ bg, float* __restrict__ Vg, float* __restrict__ hist,
+                  const float* __restrict__ last_l, et_event* events, int64_t cap,
+                  unsigned long long* n_events, float* __restrict__ I_out,
+                  int8_t* __restrict__ spikes) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  __shared__ uint64_t mma_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int bail;
+  const int L = P.L, C = P.C, kt = P.kt, R = P.R, hk = kt - 1, ks0 = P.ks0;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t npix = (int64_t)P.H * P.W;
+  const int64_t q = (int64_t)blockIdx.x * TP + tid;
+  const bool live = q < npix;
+  const int px = live ? (int)(q % P.W) : 0, py = live ? (int)(q / P.W) : 0;
+  unsigned char* rings = sm;                                   // [L-1][R] slots
+  unsigned char* wB = sm + P.off_wB;                           // [L-1][kt] 16 x 16 BF16
+  float* f32 = reinterpret_cast<float*>(sm + P.off_f32);
+  float* bs = f32;                                             // [L][CP] biases
+  float* wp = bs + L * CP;                                     // [CP] projection
+  float* bp = wp + CP;                                         // [1] (+ pad)
+  float* w0 = bp + 4;                                          // [taps][CP] layer 0
+  const int taps0 = ks0 > 0 ? ks0 * ks0 : kt;
+  float* xh = w0 + taps0 * CP;                                 // [R][TP] layer-0 X ring (temporal layer 0)
+  auto slot_of = [&](int l, int pos) { return rings + ((size_t)(l - 1) * R + pos) * kSlot; };
+  // history element (layer l, oldest-first slot j, channel c) of this pixel in the state
+  auto hidx = [&](int l, int j, int c) -> int64_t { return (((int64_t)l * hk + j) * C + c) * npix + q; };
+
+  // ---- set-up: weights, biases, history rings
+  for (int i = tid; i < L * CP; i += kThreads) {
+    const int l = i / CP, c = i % CP;
+    bs[i] = c < C ? bg[l * C + c] : 0.0f;
+  }
+  for (int i = tid; i < CP; i += kThreads) wp[i] = i < C ? wg[P.woff[L] + i] : 0.0f;
+  if (tid == 0) bp[0] = bg[L * C];
+  for (int i = tid; i < taps0 * CP; i += kThreads) {
+    const int t = i / CP, c = i % CP;
+    w0[i] = c < C ? wg[c * taps0 + t] : 0.0f;                 // layer 0: [C][1][taps]
+  }
+  // B operands: layer l >= 1, tap tau: rows n (output channel), K = input
+  // channel in two planes of 8
+  for (int i = tid; i < (L - 1) * kt * CP * CP; i += kThreads) {
+    const int k = i % CP, n = (i / CP) % CP, tau = (i / (CP * CP)) % kt, l = 1 + i / (CP * CP * kt);
+    float v = 0.0f;
+    if (n < C && k < C) v = wg[P.woff[l] + (n * C + k) * kt + tau];
+    unsigned char* dst = wB + ((size_t)(l - 1) * kt + tau) * (CP * CP * 2) + (k >> 3) * (CP * 16) + n * 16 +
+                         (k & 7) * 2;
+    *reinterpret_cast<__nv_bfloat16*>(dst) = __float2bfloat16_rn(v);
+  }
+  // ring slots of steps -(kt-1) .. -1 from the state (oldest first); others zero
+  for (int l = 1; l < L; ++l) {
+    for (int j = 0; j < hk; ++j) {
+      float v[CP];
+#pragma unroll
+      for (int c = 0; c < CP; ++c) v[c] = (live && c < C) ? hist[hidx(l, j, c)] : 0.0f;
+      store_row(slot_of(l, ring_pos(j - hk, R)), tid, v);
+    }
+  }
+  if (ks0 == 0) {
+    for (int j = 0; j < hk; ++j) xh[ring_pos(j - hk, R) * TP + tid] = live ? hist[hidx(0, j, 0)] : 0.0f;
+  }
+  float V = live ? Vg[q] : 0.0f;
+  if (warp == 0) tmem_alloc(&tmem_slot, kTmemCols);
+  if (tid == 0) { mbar_init(&mma_bar, 1); bail = 0; }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+  const uint32_t idesc = umma_idesc_bf16(TP, CP);
+  uint32_t phase = 0;
+
+  const int S = P.F - P.f0;             // steps of this call
+  for (int s0 = 0; s0 < S && !bail; s0 += kT) {
+    const int tc = min(kT, S - s0);
+    float h[kT][CP];                    // block input (residual) / current activation, FP32
+    // ---- layer 0 on CUDA cores, FP32: X_k = l_k - l_{k-1} (Eq. 1)
+#pragma unroll
+    for (int j = 0; j < kT; ++j) {
+      if (j >= tc) break;
+      const int f = P.f0 + s0 + j;
+      float acc[CP];
+#pragma unroll
+      for (int c = 0; c < CP; ++c) acc[c] = bs[c];
+      if (live) {
+        if (ks0 > 0) {
+          const int r0 = ks0 >> 1;
+          for (int dy = 0; dy < ks0; ++dy) {
+            const int yy = py + dy - r0;
+            if (yy < 0 || yy >= P.H) continue;
+            for (int dx = 0; dx < ks0; ++dx) {
+              const int xx = px + dx - r0;
+              if (xx < 0 || xx >= P.W) continue;
+              const int64_t qq = (int64_t)yy * P.W + xx;
+              const float xc = __ldg(logl + (int64_t)f * npix + qq);
+              const float xp = f == 0 ? last_l[qq] : __ldg(logl + (int64_t)(f - 1) * npix + qq);
+              const float v = xc - xp;
+              const float* wt = w0 + (dy * ks0 + dx) * CP;
+#pragma unroll
+              for (int c = 0; c < CP; ++c) acc[c] = fmaf(wt[c], v, acc[c]);
+            }
+          }
+        } else {
+          const float xc = __ldg(logl + (int64_t)f * npix + q);
+          const float xp = f == 0 ? last_l[q] : __ldg(logl + (int64_t)(f - 1) * npix + q);
+          xh[ring_pos(s0 + j, R) * TP + tid] = xc - xp;
+          for (int tau = 0; tau < kt; ++tau) {
+            const float v = xh[ring_pos(s0 + j - hk + tau, R) * TP + tid];
+            const float* wt = w0 + tau * CP;
+#pragma unroll
+            for (int c = 0; c < CP; ++c) acc[c] = fmaf(wt[c], v, acc[c]);
+          }
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < CP; ++c) h[j][c] = live ? fmaxf(acc[c], 0.0f) : 0.0f;
+      store_row(slot_of(1, ring_pos(s0 + j, R)), tid, h[j]);
+    }
+    // ---- layers 1 .. L-1 on the tensor core
+    for (int l = 1; l < L; ++l) {
+      fence_proxy_async_smem();
+      tc_fence_before();
+      __syncthreads();
+      tc_fence_after();
+      if (tid == 0) {
+        const uint32_t bbase = smem_u32(wB + (size_t)(l - 1) * kt * (CP * CP * 2));
+        for (int j = 0; j < tc; ++j)
+          for (int tau = 0; tau < kt; ++tau) {
+            const uint64_t ad = umma_desc(smem_u32(slot_of(l, ring_pos(s0 + j - hk + tau, R))), kPlane, 128);
+            const uint64_t bd = umma_desc(bbase + tau * (CP * CP * 2), CP * 16, 128);
+            umma_bf16(tmem + j * CP, ad, bd, idesc, tau != 0);
+          }
+        umma_commit(&mma_bar);
+      }
+      const bool ok = mbar_wait(&mma_bar, phase, P.wait_iters);
+      phase ^= 1;
+      if (!ok) {
+        if (lane == 0) atomicOr(n_events, kTimeoutBit);
+        bail = 1;
+      }
+      tc_fence_after();
+      __syncthreads();
+      if (bail) break;
+      const bool closing = P.kind == ET_NET_RESIDUAL && (l % 2) == 0;
+      const bool inner = P.kind == ET_NET_RESIDUAL && (l % 2) == 1;
+#pragma unroll
+      for (int j = 0; j < kT; ++j) {
+        if (j >= tc) break;
+        float acc[CP];
+        tmem_ld16(tmem + lane_base + j * CP, acc);
+        float out[CP];
+#pragma unroll
+        for (int c = 0; c < CP; ++c) {
+          const float v = acc[c] + bs[l * CP + c];
+          if (closing) { h[j][c] = fmaxf(h[j][c] + v, 0.0f); out[c] = h[j][c]; }
+          else if (inner) out[c] = fmaxf(v, 0.0f);
+          else { out[c] = fmaxf(v, 0.0f); h[j][c] = out[c]; }
+          if (!live) out[c] = 0.0f;
+        }
+        if (l + 1 < L) store_row(slot_of(l + 1, ring_pos(s0 + j, R)), tid, out);
+        else {
+#pragma unroll
+          for (int c = 0; c < CP; ++c) h[j][c] = out[c];
+        }
+      }
+      tc_fence_before();
+    }
+    if (bail) break;
+    // ---- Eq. 6 projection and BiLIF, step by step
+#pragma unroll
+    for (int j = 0; j < kT; ++j) {
+      if (j >= tc) break;
+      const int f = P.f0 + s0 + j;
+      uint32_t nev = 0;
+      int Sp = 0;
+      if (live) {
+        float I = bp[0];
+#pragma unroll
+        for (int c = 0; c < CP; ++c) I = fmaf(wp[c], h[j][c], I);
+        const float vp = P.beta * V + I;
+        Sp = vp >= P.vth ? 1 : (vp <= -P.vth ? -1 : 0);
+        V = vp - P.reset * (float)Sp;
+        nev = (Sp != 0 && P.t0 + f >= 0) ? 1u : 0u;   // delayed labels below 0: none
+        const int64_t o = (int64_t)(s0 + j) * npix + q;
+        if (I_out) I_out[o] = I;
+        if (spikes) spikes[o] = (int8_t)Sp;
+      }
+      emit_events_warp(events, cap, n_events, nev, (uint32_t)px, (uint32_t)py, (uint32_t)(P.t0 + f), Sp);
+    }
+  }
+  __syncthreads();
+  if (bail) {
+    // a bounded wait gave up: give the MMAs still in flight a second bounded wait
+    mbar_wait(&mma_bar, phase ^ 1u, P.wait_iters);
+  } else if (live) {
+    Vg[q] = V;
+    // the last kt - 1 inputs of every layer back to the state, oldest first
+    for (int l = 1; l < L; ++l)
+      for (int j = 0; j < hk; ++j) {
+        float v[CP];
+        load_row(slot_of(l, ring_pos(S - hk + j, R)), tid, v);
+        for (int c = 0; c < C; ++c) hist[hidx(l, j, c)] = v[c];
+      }
+    if (ks0 == 0)
+      for (int j = 0; j < hk; ++j) hist[hidx(0, j, 0)] = xh[ring_pos(S - hk + j, R) * TP + tid];
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tmem, kTmemCols);
+}
+
+}  // namespace
+
+// BF16 tensor-core path of the pixel-wise form; declines (before launching
+// anything) what it does not cover.
+int et_evsnet_forward_tct(const float* logl, int32_t F, const et_evsnet_weights* net,
+                          et_evsnet_state* st, int32_t t0, et_event* events, int64_t cap,
+                          int64_t* n_events, float* I_out, int8_t* spikes, cudaStream_t stream) {
+  if (net->dtype != ET_BF16 || net->ks != 1 || net->C > CP || net->kt > kMaxKt || net->ks0 > kMaxStem ||
+      net->n_layers < 2)
+    return ET_ERR_UNIMPLEMENTED;
+  TctParams P{};
+  P.H = st->H; P.W = st->W; P.F = F; P.f0 = st->initialized ? 0 : 1; P.t0 = t0;
+  P.L = net->n_layers; P.C = net->C; P.kt = net->kt; P.ks0 = net->ks0; P.kind = net->kind;
+  P.beta = net->beta; P.vth = net->vth; P.reset = net->reset;
+  P.R = P.kt + kT - 1;
+  int wo = 0;
+  for (int l = 0; l < P.L; ++l) {
+    P.woff[l] = wo;
+    wo += l == 0 ? P.C * (P.ks0 > 0 ? P.ks0 * P.ks0 : P.kt) : P.C * P.C * P.kt;
+  }
+  P.woff[P.L] = wo;
+  P.wait_iters = et_tc_wait_iters();
+  const size_t rings = (size_t)(P.L - 1) * P.R * kSlot;
+  const size_t wbytes = (size_t)(P.L - 1) * P.kt * CP * CP * 2;
+  const int taps0 = P.ks0 > 0 ? P.ks0 * P.ks0 : P.kt;
+  const size_t fbytes = sizeof(float) * ((size_t)P.L * CP + CP + 4 + (size_t)taps0 * CP + (size_t)P.R * TP);
+  P.off_wB = (int)rings;
+  P.off_f32 = (int)(rings + wbytes);
+  const size_t smem = rings + wbytes + fbytes;
+  int dev = 0, max_smem = 0;
+  ET_CHECK_CUDA(cudaGetDevice(&dev));
+  ET_CHECK_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  // static shared memory (barrier, TMEM slot, flag) comes on top of the dynamic part
+  if (smem + 1024 > (size_t)max_smem) return ET_ERR_UNIMPLEMENTED;
+  if (P.kt > 1 && !st->hist) return ET_ERR_ARG;
+  ET_CHECK_CUDA(cudaFuncSetAttribute(evsnet_tct_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int64_t npix = (int64_t)P.H * P.W;
+  evsnet_tct_kernel<<<(unsigned)((npix + TP - 1) / TP), kThreads, smem, stream>>>(
+      P, logl, net->w, net->b, st->V, st->hist, st->last_l, events, cap,
+      reinterpret_cast<unsigned long long*>(n_events), I_out, spikes);
+  ET_CHECK_LAUNCH();
+  return ET_OK;
+}

@@ -429,6 +429,8 @@ extern "C" void et_scene_free(et_scene* s) {
   cudaFree(s->d_perm);
   cudaFree(s->d_refit);
   cudaFree(s->d_upd);
+  for (cudaEvent_t e : s->prof.pool) cudaEventDestroy(e);
+  if (s->prof.h_len) cudaFreeHost(s->prof.h_len);
   delete s;
 }
 

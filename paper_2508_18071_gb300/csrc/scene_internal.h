@@ -3,6 +3,22 @@
 #include <vector>
 #include "et_internal.cuh"
 
+// Per-kernel timing of the wavefront schedule (et_render_profile): events
+// around each launch and the queue lengths each launch processed, copied to
+// pinned host memory; summed by et_render_profile_read.
+struct RenderProf {
+  static constexpr int kKinds = 5;        // raygen, trace, shade, shadow, accumulate
+  static constexpr int kSlots = 1 << 15;  // queue-length copies held between reads
+  bool on = false;
+  std::vector<cudaEvent_t> pool;          // events, reused across reads
+  size_t used = 0;
+  struct Mark { int kind; size_t e0, e1; int slot; int64_t items; };
+  std::vector<Mark> marks;
+  uint32_t* h_len = nullptr;              // pinned: queue lengths read by the device
+  int n_len = 0;
+  bool overflow = false;
+};
+
 struct et_scene {
   float4* d_tris = nullptr;
   BvhNode* d_nodes = nullptr;
@@ -24,4 +40,5 @@ struct et_scene {
   int32_t* d_refit = nullptr;
   std::vector<int> refit_levels;
   float* d_upd = nullptr;
+  RenderProf prof;
 };

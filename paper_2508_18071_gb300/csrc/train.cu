@@ -605,7 +605,8 @@ int check(const et_evsnet_weights* net, const et_train_shape* sh) {
   if (!net || !sh || !net->w || !net->b) return ET_ERR_ARG;
   if (sh->B < 1 || sh->K < 1 || sh->H < 1 || sh->W < 1 || sh->ckpt_every < 1) return ET_ERR_ARG;
   if (net->n_layers < 1 || net->n_layers > kMaxLayers || net->C < 1) return ET_ERR_UNIMPLEMENTED;
-  const bool spatial = net->kind == ET_NET_STACK && net->ks == 3 && net->kt == 1 && net->C <= kMaxC;
+  const bool spatial = net->kind == ET_NET_STACK && net->ks == 3 && net->kt == 1 && net->C <= kMaxC &&
+                       net->ks0 == 0;
   if (!spatial && !et_train_is_temporal(net)) return ET_ERR_UNIMPLEMENTED;
   // BF16: the spatial form's C -> C convolutions on the tensor cores
   if (net->dtype != ET_F32 && !(net->dtype == ET_BF16 && spatial)) return ET_ERR_UNIMPLEMENTED;

@@ -24,8 +24,13 @@ constexpr int kMaxC = 16;
 constexpr int kMaxKt = 9;
 constexpr float kPi = 3.14159265358979323846f;
 
-__host__ __device__ inline int64_t twofs(int l, int C, int kt) {
-  return l == 0 ? 0 : (int64_t)C * kt + (int64_t)(l - 1) * C * C * kt;
+// packed weight offset of layer l; n0 = weights per output channel of layer 0
+// (kt, or ks0 * ks0 for a spatial stem)
+inline int64_t twofs(int l, int C, int kt, int n0) {
+  return l == 0 ? 0 : (int64_t)C * n0 + (int64_t)(l - 1) * C * C * kt;
+}
+inline int layer0_taps(const et_evsnet_weights* net) {
+  return net->ks0 > 0 ? net->ks0 * net->ks0 : net->kt;
 }
 
 // ------------------------------------------------------- forward conv, layer 0
@@ -54,6 +59,54 @@ tconv_fwd(const float* __restrict__ logl, int B, int K, int64_t hw, int C, int k
 #pragma unroll
     for (int co = 0; co < kMaxC; ++co)
       if (co < C) acc[co] += sw[co * kt + tau] * x;
+  }
+  float* dst = out + idx * C;
+  float Iv = bp ? bp[0] : 0.0f;
+#pragma unroll
+  for (int co = 0; co < kMaxC; ++co) {
+    if (co >= C) break;
+    const float a = fmaxf(acc[co], 0.0f);
+    dst[co] = a;
+    if (I) Iv += wp[co] * a;
+  }
+  if (I) I[idx] = Iv;
+}
+
+// ------------------------------------------------- forward, spatial stem
+// Layer 0 as a one-step ks0 x ks0 convolution of X (zero outside the image);
+// one thread per (clip, step, pixel), taps in row-major order.
+constexpr int kMaxStem = 7;
+__global__ void __launch_bounds__(256, 4)
+tstem_fwd(const float* __restrict__ logl, int B, int K, int H, int W, int C, int ks0,
+          const float* __restrict__ w, const float* __restrict__ b, float* __restrict__ out,
+          const float* __restrict__ wp, const float* __restrict__ bp, float* __restrict__ I) {
+  __shared__ float sw[kMaxStem * kMaxStem][kMaxC];   // [tap][co]
+  for (int i = threadIdx.x; i < C * ks0 * ks0; i += blockDim.x) sw[i % (ks0 * ks0)][i / (ks0 * ks0)] = w[i];
+  __syncthreads();
+  const int64_t hw = (int64_t)H * W;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)B * K * hw) return;
+  const int64_t p = idx % hw;
+  const int k = (int)((idx / hw) % K), bc = (int)(idx / (hw * K));
+  const int y = (int)(p / W), x = (int)(p % W), r0 = ks0 >> 1;
+  const float* l1 = logl + ((int64_t)bc * (K + 1) + k + 1) * hw;
+  const float* l0 = l1 - hw;
+  float acc[kMaxC];
+#pragma unroll
+  for (int co = 0; co < kMaxC; ++co) acc[co] = co < C ? b[co] : 0.0f;
+  for (int dy = 0; dy < ks0; ++dy) {
+    const int yy = y + dy - r0;
+    if (yy < 0 || yy >= H) continue;
+    for (int dx = 0; dx < ks0; ++dx) {
+      const int xx = x + dx - r0;
+      if (xx < 0 || xx >= W) continue;
+      const int64_t q = (int64_t)yy * W + xx;
+      const float v = l1[q] - l0[q];
+      const float* wt = sw[dy * ks0 + dx];
+#pragma unroll
+      for (int co = 0; co < kMaxC; ++co)
+        if (co < C) acc[co] = fmaf(wt[co], v, acc[co]);
+    }
   }
   float* dst = out + idx * C;
   float Iv = bp ? bp[0] : 0.0f;
@@ -227,6 +280,72 @@ tconv_bwd_weight(const float* __restrict__ dz, const float* __restrict__ logl, i
     if (e >= nent) break;
     if (e < C * Cin * kt) atomicAdd(gw + e, acc[j]);
     else atomicAdd(gb + (e - C * Cin * kt), acc[j]);
+  }
+}
+
+// -------------------------------------- weight backward, spatial stem
+// grad w[co][tap] += sum dz[k][co] X_nbr(tap)[k]; grad b[co] += sum dz[k][co]:
+// the layer-0 kernel above with the taps running over the ks0 x ks0
+// neighbourhood of the current step instead of over time.
+__global__ void __launch_bounds__(256)
+tstem_bwd_weight(const float* __restrict__ dz, const float* __restrict__ logl, int B, int K, int H,
+                 int W, int C, int ks0, float* __restrict__ gw, float* __restrict__ gb) {
+  constexpr int kTaps = kMaxStem * kMaxStem;
+  __shared__ float sd[kPts][kMaxC];
+  __shared__ float sx[kPts][kTaps + 1];
+  constexpr int kPer = (kMaxC * kTaps + kMaxC + 255) / 256;
+  float acc[kPer];
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) acc[j] = 0.0f;
+  const int nt = ks0 * ks0, r0 = ks0 >> 1;
+  const int nent = C * nt + C;
+  const int64_t hw = (int64_t)H * W;
+  const int64_t npts = (int64_t)B * K * hw;
+  for (int64_t c0 = (int64_t)blockIdx.x * kPts; c0 < npts; c0 += (int64_t)gridDim.x * kPts) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < kPts * C; i += blockDim.x) {
+      const int pt = i / C, co = i % C;
+      const int64_t idx = c0 + pt;
+      sd[pt][co] = idx < npts ? dz[idx * C + co] : 0.0f;
+    }
+    for (int i = threadIdx.x; i < kPts * nt; i += blockDim.x) {
+      const int pt = i / nt, tap = i % nt;
+      const int64_t idx = c0 + pt;
+      float v = 0.0f;
+      if (idx < npts) {
+        const int64_t p = idx % hw;
+        const int k = (int)((idx / hw) % K), bc = (int)(idx / (hw * K));
+        const int yy = (int)(p / W) + tap / ks0 - r0, xx = (int)(p % W) + tap % ks0 - r0;
+        if (yy >= 0 && yy < H && xx >= 0 && xx < W) {
+          const float* l1 = logl + ((int64_t)bc * (K + 1) + k + 1) * hw;
+          const int64_t q = (int64_t)yy * W + xx;
+          v = l1[q] - l1[q - hw];
+        }
+      }
+      sx[pt][tap] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+      const int e = threadIdx.x + j * 256;
+      if (e >= nent) break;
+      float s = 0.0f;
+      if (e < C * nt) {
+        const int co = e / nt, tap = e % nt;
+        for (int pt = 0; pt < kPts; ++pt) s += sd[pt][co] * sx[pt][tap];
+      } else {
+        const int co = e - C * nt;
+        for (int pt = 0; pt < kPts; ++pt) s += sd[pt][co];
+      }
+      acc[j] += s;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    const int e = threadIdx.x + j * 256;
+    if (e >= nent) break;
+    if (e < C * nt) atomicAdd(gw + e, acc[j]);
+    else atomicAdd(gb + (e - C * nt), acc[j]);
   }
 }
 
@@ -517,16 +636,21 @@ int tforward(const float* logl, const et_train_shape* sh, const et_evsnet_weight
   const int64_t hw = (int64_t)sh->H * sh->W, n = (int64_t)sh->B * sh->K * hw;
   const unsigned grid = (unsigned)((n + 255) / 256);
   const unsigned grid2 = (unsigned)(((int64_t)sh->B * ((sh->K + 1) / 2) * hw + 255) / 256);   // step pairs
-  const float* wp = net->w + twofs(L, C, kt);
+  const int n0 = layer0_taps(net);
+  const float* wp = net->w + twofs(L, C, kt, n0);
   const float* bp = net->b + (int64_t)L * C;
-  tconv_fwd<<<grid, 256, 0, st>>>(logl, sh->B, sh->K, hw, C, kt, net->w, net->b, ws.act[0], wp, bp,
-                                  L == 1 ? ws.I : nullptr);
+  if (net->ks0 > 0)
+    tstem_fwd<<<grid, 256, 0, st>>>(logl, sh->B, sh->K, sh->H, sh->W, C, net->ks0, net->w, net->b,
+                                    ws.act[0], wp, bp, L == 1 ? ws.I : nullptr);
+  else
+    tconv_fwd<<<grid, 256, 0, st>>>(logl, sh->B, sh->K, hw, C, kt, net->w, net->b, ws.act[0], wp, bp,
+                                    L == 1 ? ws.I : nullptr);
   ET_CHECK_LAUNCH();
   for (int l = 1; l < L; ++l) {
     // residual form: even layers close a block and add its input
     const float* res = (net->kind == ET_NET_RESIDUAL && l % 2 == 0) ? ws.act[l - 2] : nullptr;
     auto kern = C == CP ? tconv16_fwd<true> : tconv16_fwd<false>;
-    kern<<<grid2, 256, 0, st>>>(ws.act[l - 1], sh->B, sh->K, hw, C, kt, net->w + twofs(l, C, kt),
+    kern<<<grid2, 256, 0, st>>>(ws.act[l - 1], sh->B, sh->K, hw, C, kt, net->w + twofs(l, C, kt, n0),
                                net->b + (int64_t)l * C, res, ws.act[l], wp, bp,
                                l == L - 1 ? ws.I : nullptr);
     ET_CHECK_LAUNCH();
@@ -537,7 +661,8 @@ int tforward(const float* logl, const et_train_shape* sh, const et_evsnet_weight
 }  // namespace
 
 bool et_train_is_temporal(const et_evsnet_weights* net) {
-  return net->ks == 1 && net->kt >= 1 && net->kt <= kMaxKt && net->C <= kMaxC &&
+  const bool stem_ok = net->ks0 == 0 || (net->ks0 > 0 && net->ks0 <= kMaxStem && net->ks0 % 2 == 1);
+  return net->ks == 1 && net->kt >= 1 && net->kt <= kMaxKt && net->C <= kMaxC && stem_ok &&
          (net->kind == ET_NET_STACK || (net->kind == ET_NET_RESIDUAL && net->n_layers % 2 == 1));
 }
 
@@ -585,8 +710,9 @@ int et_train_temporal_backward(const float* logl, const et_train_shape* sh,
   const unsigned grid2 = (unsigned)((npx * ((K + 1) / 2) + 255) / 256);   // step pairs
   const unsigned wgrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(nsm * 8, (n + kPts - 1) / kPts));
   float* dz = ws.g[0];
-  tproj_bwd<<<nsm * 4, 256, 0, st>>>(ws.dI, ws.act[L - 1], n, C, net->w + twofs(L, C, kt), dz,
-                                     grad_w + twofs(L, C, kt), grad_b + (int64_t)L * C);
+  const int n0 = layer0_taps(net);
+  tproj_bwd<<<nsm * 4, 256, 0, st>>>(ws.dI, ws.act[L - 1], n, C, net->w + twofs(L, C, kt, n0), dz,
+                                     grad_w + twofs(L, C, kt, n0), grad_b + (int64_t)L * C);
   ET_CHECK_LAUNCH();
   const int wthr = twgrad_threads(kt);
   const size_t wsmem = sizeof(float) * kPts16 * CP * (1 + kt);
@@ -597,10 +723,12 @@ int et_train_temporal_backward(const float* logl, const et_train_shape* sh,
       1, std::min<int64_t>((int64_t)nsm * std::max(wblocks, 1), (n + kPts16 - 1) / kPts16));
   auto dkern = C == CP ? tconv16_bwd_data<true> : tconv16_bwd_data<false>;
   auto wgrad = [&](const float* d, int l) {
-    if (l == 0)
+    if (l == 0 && net->ks0 > 0)
+      tstem_bwd_weight<<<wgrid, 256, 0, st>>>(d, logl, B, K, sh->H, sh->W, C, net->ks0, grad_w, grad_b);
+    else if (l == 0)
       tconv_bwd_weight<<<wgrid, 256, 0, st>>>(d, logl, B, K, hw, C, kt, grad_w, grad_b);
     else
-      wkern<<<wgrid16, wthr, wsmem, st>>>(d, ws.act[l - 1], B, K, hw, C, kt, grad_w + twofs(l, C, kt),
+      wkern<<<wgrid16, wthr, wsmem, st>>>(d, ws.act[l - 1], B, K, hw, C, kt, grad_w + twofs(l, C, kt, n0),
                                           grad_b + (int64_t)l * C);
   };
   if (net->kind == ET_NET_STACK) {
@@ -609,7 +737,7 @@ int et_train_temporal_backward(const float* logl, const et_train_shape* sh,
       wgrad(ws.g[cur], l);
       ET_CHECK_LAUNCH();
       if (l > 0) {
-        dkern<<<grid2, 256, 0, st>>>(ws.g[cur], B, K, hw, C, kt, net->w + twofs(l, C, kt), nullptr,
+        dkern<<<grid2, 256, 0, st>>>(ws.g[cur], B, K, hw, C, kt, net->w + twofs(l, C, kt, n0), nullptr,
                                     ws.act[l - 1], ws.g[cur ^ 1]);
         ET_CHECK_LAUNCH();
         cur ^= 1;
@@ -625,13 +753,13 @@ int et_train_temporal_backward(const float* logl, const et_train_shape* sh,
     wgrad(ws.g[cz], lc);
     ET_CHECK_LAUNCH();
     // dy = conv_lc^T(dz) masked by a > 0
-    dkern<<<grid2, 256, 0, st>>>(ws.g[cz], B, K, hw, C, kt, net->w + twofs(lc, C, kt), nullptr,
+    dkern<<<grid2, 256, 0, st>>>(ws.g[cz], B, K, hw, C, kt, net->w + twofs(lc, C, kt, n0), nullptr,
                                 ws.act[la], ws.g[cy]);
     ET_CHECK_LAUNCH();
     wgrad(ws.g[cy], la);
     ET_CHECK_LAUNCH();
     // dz_prev = (dz + conv_la^T(dy)) masked by h_{i-1} > 0
-    dkern<<<grid2, 256, 0, st>>>(ws.g[cy], B, K, hw, C, kt, net->w + twofs(la, C, kt), ws.g[cz],
+    dkern<<<grid2, 256, 0, st>>>(ws.g[cy], B, K, hw, C, kt, net->w + twofs(la, C, kt, n0), ws.g[cz],
                                 ws.act[la - 1], ws.g[cn]);
     ET_CHECK_LAUNCH();
     cz = cn;

@@ -27,6 +27,13 @@ constexpr unsigned FULL = 0xFFFFFFFFu;
 constexpr int kLeafBatch = 24;       // lanes waiting at leaves that end a node phase
 constexpr int kNodeSteps = 3;        // node visits per lane between two warp votes
 constexpr int64_t kPathCap = 8 << 20;
+// et_render_profile kinds (the order of the ms / launches / items arrays)
+enum { kProfRaygen = 0, kProfTrace = 1, kProfShade = 2, kProfShadow = 3, kProfAccumulate = 4 };
+#define ET_TRY(expr)                 \
+  do {                               \
+    const int rc_ = (expr);          \
+    if (rc_ != ET_OK) return rc_;    \
+  } while (0)
 
 enum { C_NRAY0 = 0, C_NRAY1 = 1, C_NSH = 2, C_FETCH = 3, C_FETCH_SH = 4, C_N = 8 };
 
@@ -41,6 +48,7 @@ struct Args {
   et_scene_dev S;
   const et_camera* cams;
   int W, H, spp, max_depth;
+  int y0;              // first image row of the rendered band (pixel ids are band-relative)
   uint32_t first_frame, k0, k1;
   Batch bt;
   float4* beta_pdf;
@@ -87,7 +95,7 @@ __global__ void __launch_bounds__(256) wf_raygen(Args A) {
   int f, s;
   int64_t pix;
   path_ids(A.bt, q, f, s, pix);
-  const int x = (int)(pix % A.W), y = (int)(pix / A.W);
+  const int x = (int)(pix % A.W), y = (int)(pix / A.W) + A.y0;
   const pt::Cam cam = pt::load_cam(A.cams[f]);
   f3 o, d;
   pt::camera_ray(cam, A.W, A.H, x, y, (uint32_t)s, A.first_frame + (uint32_t)f, A.k0, A.k1, o, d);
@@ -215,7 +223,7 @@ __global__ void __launch_bounds__(256) wf_shade(Args A, int cur, int b) {
       const bool cont = pt::arrive(A.S, o, d, h, b, A.max_depth, bp.w, beta, L, v);
       A.L[q] = make_float4(L.x, L.y, L.z, 0.0f);
       if (cont) {
-        const uint32_t pixu = (uint32_t)pix, frame = A.first_frame + (uint32_t)f;
+        const uint32_t pixu = (uint32_t)(pix + (int64_t)A.y0 * A.W), frame = A.first_frame + (uint32_t)f;
         if (A.S.n_lights > 0)
           want_sh = pt::nee(A.S, v, pixu, (uint32_t)s, frame, b, A.k0, A.k1, beta, sh_dir, sh_tmax,
                             contrib, light);
@@ -274,10 +282,10 @@ int ensure_workspace(et_scene* s, int64_t paths, int64_t acc_pix) {
 
 }  // namespace
 
-int et_render_wavefront(et_scene* s, int n_frames, int first_frame, int W, int H, int spp,
-                        int max_depth, uint64_t seed, float* rgb, float* logl, int log_mode,
+int et_render_wavefront(et_scene* s, int n_frames, int first_frame, int W, int H, int y0, int y1,
+                        int spp, int max_depth, uint64_t seed, float* rgb, float* logl, int log_mode,
                         float log_param, int32_t* records, cudaStream_t stream) {
-  const int64_t npix = (int64_t)W * H;
+  const int64_t npix = (int64_t)W * (y1 - y0);
   const int64_t planes = std::max<int64_t>(1, kPathCap / npix);
   Batch proto{};
   proto.npix = npix;
@@ -297,7 +305,7 @@ int et_render_wavefront(et_scene* s, int n_frames, int first_frame, int W, int H
   Args A{};
   A.S = s->dev;
   A.cams = s->d_cams;
-  A.W = W; A.H = H; A.spp = spp; A.max_depth = max_depth;
+  A.W = W; A.H = H; A.spp = spp; A.max_depth = max_depth; A.y0 = y0;
   A.first_frame = (uint32_t)first_frame;
   A.k0 = (uint32_t)seed; A.k1 = (uint32_t)(seed >> 32);
   A.records = records;
@@ -328,27 +336,38 @@ int et_render_wavefront(et_scene* s, int n_frames, int first_frame, int W, int H
       bt.paths = (int64_t)nf * bt.ns * npix;
       A.bt = bt;
       ET_CHECK_CUDA(cudaMemsetAsync(A.ctr, 0, sizeof(uint32_t) * C_N, stream));
+      size_t pe = 0;   // profiling marks (et_render_profile; no-ops when off)
+      ET_TRY(prof_begin(s, kProfRaygen, stream, &pe));
       wf_raygen<<<(unsigned)((bt.paths + 255) / 256), 256, 0, stream>>>(A);
       ET_CHECK_LAUNCH();
+      ET_TRY(prof_end(s, kProfRaygen, pe, bt.paths, nullptr, stream));
       int cur = 0;
       for (int b = 1; b <= max_depth; ++b) {
         const int nxt = cur ^ 1;
         ET_CHECK_CUDA(cudaMemsetAsync(A.ctr + C_NRAY0 + nxt, 0, sizeof(uint32_t), stream));
         ET_CHECK_CUDA(cudaMemsetAsync(A.ctr + C_NSH, 0, sizeof(uint32_t) * 3, stream));
+        ET_TRY(prof_begin(s, kProfTrace, stream, &pe));
         wf_trace<false><<<grid_c, 128, 0, stream>>>(A, cur, b);
         ET_CHECK_LAUNCH();
+        ET_TRY(prof_end(s, kProfTrace, pe, 0, A.ctr + C_NRAY0 + cur, stream));
+        ET_TRY(prof_begin(s, kProfShade, stream, &pe));
         wf_shade<<<grid_shade, 256, 0, stream>>>(A, cur, b);
         ET_CHECK_LAUNCH();
+        ET_TRY(prof_end(s, kProfShade, pe, 0, A.ctr + C_NRAY0 + cur, stream));
         if (s->dev.n_lights > 0 && b < max_depth) {
+          ET_TRY(prof_begin(s, kProfShadow, stream, &pe));
           wf_trace<true><<<grid_s, 128, 0, stream>>>(A, cur, b);
           ET_CHECK_LAUNCH();
+          ET_TRY(prof_end(s, kProfShadow, pe, 0, A.ctr + C_NSH, stream));
         }
         cur = nxt;
       }
       const int64_t np = (int64_t)nf * npix;
+      ET_TRY(prof_begin(s, kProfAccumulate, stream, &pe));
       wf_accumulate<<<(unsigned)((np + 255) / 256), 256, 0, stream>>>(
           A, acc, s0 == 0, s0 + bt.ns >= spp, rgb, logl, log_mode, log_param);
       ET_CHECK_LAUNCH();
+      ET_TRY(prof_end(s, kProfAccumulate, pe, np, nullptr, stream));
     }
   }
   return ET_OK;

@@ -17,6 +17,11 @@ The one exchange step is the final gather of the event lists: an all_gather of
 the per-rank counts, then an all_gather of the (padded) event arrays, with the
 band offset added to y.  Rows are returned sorted by (t, y, x, p) so that the
 sharded result is bitwise the unsharded one.
+
+Training is data-parallel over clips: every rank computes the gradient of the
+loss on its own clips and one all_reduce makes the mean over ranks.  The loss
+(Eq. 7-11) is a mean over the batch's pixels, so with equal shards the mean of
+the ranks' gradients is the whole batch's gradient.
 """
 from __future__ import annotations
 
@@ -69,3 +74,22 @@ def gather_events(local: np.ndarray, y_offset: int = 0, group=None) -> np.ndarra
     dist.all_gather(parts, buf, group=group)
     full = np.concatenate([p[: int(c.item())].numpy() for p, c in zip(parts, counts)])
     return sort_events(full)
+
+
+def allreduce_mean(tensors, group=None):
+    """Mean over ranks of each tensor, in place (one all_reduce for all of them:
+    they are flattened into one buffer).  With the gloo backend the buffer goes
+    through host memory."""
+    import torch
+    import torch.distributed as dist
+    world = dist.get_world_size(group)
+    flat = torch.cat([t.reshape(-1) for t in tensors])
+    buf = flat.cpu() if dist.get_backend(group) == "gloo" else flat
+    dist.all_reduce(buf, op=dist.ReduceOp.SUM, group=group)
+    buf = buf.to(flat.device) / world
+    o = 0
+    for t in tensors:
+        n = t.numel()
+        t.copy_(buf[o:o + n].reshape(t.shape))
+        o += n
+    return tensors

@@ -29,8 +29,7 @@ def _shape(B, K, H, W, ckpt_every):
 def _net_struct(meta: EvsNetDev, w: torch.Tensor, b: torch.Tensor):
     # weights stay FP32; meta.dtype = ET_BF16 runs the 3x3 C -> C convolutions
     # (forward and data gradient) on the tensor cores with BF16 operands
-    return L.et_evsnet_weights(meta.kind, meta.n_layers, meta.C, meta.kt, meta.ks, meta.beta,
-                               meta.vth, meta.reset, meta.dtype, w.data_ptr(), b.data_ptr())
+    return meta.c_struct(w, b)
 
 
 class Workspace:
@@ -175,14 +174,20 @@ class Trainer:
         self.lr, self.lam, self.alpha, self.ckpt = lr, lam, alpha, ckpt_every
         self.t = 0
 
-    def step(self, logl: torch.Tensor, E: torch.Tensor) -> torch.Tensor:
-        """One update on a batch; returns the device loss [3] (before the update)."""
+    def step(self, logl: torch.Tensor, E: torch.Tensor, group=None) -> torch.Tensor:
+        """One update on a batch; returns the device loss [3] (before the update).
+        With a process group (data parallelism over clips: every rank passes its
+        own equal share of the batch), the gradients are averaged over the ranks
+        by one all_reduce before Adam, so every rank applies the same update."""
         out = train_forward(logl, self.meta, self.w, self.b, ckpt_every=self.ckpt, want_S=False)
         loss, dSon, dSoff = emd_count_loss(out["spikes"], E, self.lam)
         self.gw.zero_()
         self.gb.zero_()
         train_backward(logl, self.meta, self.w, self.b, out["V_ckpt"], dSon, dSoff, self.ckpt,
                        self.alpha, self.gw, self.gb)
+        if group is not None:
+            from .sharding import allreduce_mean
+            allreduce_mean([self.gw, self.gb], group)
         self.t += 1
         adam_step(self.w, self.gw, self.mw, self.vw, self.t, self.lr)
         adam_step(self.b, self.gb, self.mb, self.vb, self.t, self.lr)
@@ -194,15 +199,17 @@ class Trainer:
         np.savez(path, w=self.w.cpu().numpy(), b=self.b.cpu().numpy(), mw=self.mw.cpu().numpy(),
                  vw=self.vw.cpu().numpy(), mb=self.mb.cpu().numpy(), vb=self.vb.cpu().numpy(),
                  t=self.t, lr=self.lr, lam=self.lam, alpha=self.alpha, ckpt=self.ckpt,
-                 meta=np.array([m.kind, m.n_layers, m.C, m.kt, m.ks]), dtype=m.dtype,
+                 meta=np.array([m.kind, m.n_layers, m.C, m.kt, m.ks, m.ks0, m.delay]), dtype=m.dtype,
                  lif=np.array([m.beta, m.vth, m.reset], np.float64))
 
     @staticmethod
     def load(path: str) -> "Trainer":
         z = np.load(path)
-        kind, n_layers, C, kt, ks = (int(v) for v in z["meta"])
+        meta = [int(v) for v in z["meta"]] + [0, 0]
+        kind, n_layers, C, kt, ks, ks0, delay = meta[:7]
         beta, vth, reset = (float(v) for v in z["lif"])
-        net = {"kind": kind, "n_layers": n_layers, "C": C, "kt": kt, "ks": ks, "beta": beta,
+        net = {"kind": kind, "n_layers": n_layers, "C": C, "kt": kt, "ks": ks, "ks0": ks0,
+               "delay": delay, "beta": beta,
                "vth": vth, "reset": reset, "w": z["w"], "b": z["b"]}
         T = Trainer(net, lr=float(z["lr"]), lam=float(z["lam"]), alpha=float(z["alpha"]),
                     ckpt_every=int(z["ckpt"]), dtype=int(z["dtype"]) if "dtype" in z else L.ET_F32)
@@ -214,6 +221,6 @@ class Trainer:
     def net_dict(self) -> dict:
         m = self.meta
         return {"kind": m.kind, "n_layers": m.n_layers, "C": m.C, "kt": m.kt, "ks": m.ks,
-                "beta": m.beta, "vth": m.vth, "reset": m.reset,
+                "ks0": m.ks0, "delay": m.delay, "beta": m.beta, "vth": m.vth, "reset": m.reset,
                 "w": self.w.detach().cpu().numpy().astype(np.float32),
                 "b": self.b.detach().cpu().numpy().astype(np.float32)}

@@ -80,8 +80,7 @@ def test_threshold_full_size(api, orc):
 
 # ------------------------------------------------------------------ EvSNet
 def _net(orc, d):
-    return orc.EvsNet(d["kind"], d["n_layers"], d["C"], d["kt"], d["ks"], d["beta"], d["vth"],
-                      d["reset"], np.asarray(d["w"], np.float64), np.asarray(d["b"], np.float64))
+    return orc.EvsNet.from_dict(d)
 
 
 def _check_evsnet(api, orc, d, lf, chunks=None, margin_tol=1e-5, max_tie_frac=0.02):
@@ -138,8 +137,24 @@ def test_evsnet_paper_form_kernel7_residual(api, orc):
     assert len(oev) > 50
 
 
-@pytest.mark.parametrize("form", [(0, 2, 2, 1, 3), (0, 4, 16, 1, 3), (1, 7, 16, 7, 1), (1, 7, 2, 7, 1)],
-                         ids=["3x3_L2_C2", "3x3_L4_C16", "temporal_k7_M3_C16", "temporal_k7_M3_C2"])
+@pytest.mark.parametrize("ks0,C,H,W,delay", [(3, 16, 19, 21, 0), (5, 16, 37, 45, 6), (3, 8, 11, 130, 21),
+                                             (7, 16, 13, 9, 2)])
+def test_evsnet_spatial_stem_then_temporal_blocks(api, orc, ks0, C, H, W, delay):
+    """A spatial stem (layer 0 one step by ks0 x ks0) ahead of the paper's
+    temporal residual blocks (kernel 7, M = 3): ragged sizes, streamed in three
+    chunks (the neighbours' previous frame then comes from the state), events
+    labelled with a delay -- against the oracle."""
+    d = inputs.random_evsnet(1, 7, C, 7, 1, seed=5 + ks0, vth=0.3, beta=0.95, ks0=ks0, delay=delay)
+    lf = inputs.random_logl_clip(16 + ks0, 30, H, W, step_std=0.3)
+    ev, oev = _check_evsnet(api, orc, d, lf, chunks=[(0, 5), (5, 6), (6, 30)])
+    assert len(oev) > 10
+    assert ev[:, 2].min() >= 0 and oev[:, 2].max() <= 29 - delay
+
+
+@pytest.mark.parametrize("form", [(0, 2, 2, 1, 3, 0), (0, 4, 16, 1, 3, 0), (1, 7, 16, 7, 1, 0),
+                                  (1, 7, 2, 7, 1, 0), (1, 7, 16, 7, 1, 3)],
+                         ids=["3x3_L2_C2", "3x3_L4_C16", "temporal_k7_M3_C16", "temporal_k7_M3_C2",
+                              "stem3_temporal_k7_M3_C16"])
 def test_identity_evsnet_equals_gpu_threshold(api, orc, form):
     """P6: the hand-set identity network with beta = 1, Vth = reset = C reproduces
     the threshold generator while steps stay below C -- for stacks of 3x3
@@ -156,7 +171,7 @@ def test_identity_evsnet_equals_gpu_threshold(api, orc, form):
     dl = torch.as_tensor(lf).cuda()
     ref = torch.zeros(H * W, dtype=torch.float64, device="cuda")
     thr = api.threshold_events(dl, C, ref, False).host()
-    d = inputs.identity_evsnet(*form, vth=C)
+    d = inputs.identity_evsnet(*form[:5], vth=C, ks0=form[5])
     onet = _net(orc, d)
     _, _, mg = orc.evsnet_forward(lf, onet, orc.EvsState.new(onet, H, W), want_margin=True)
     gnet = api.EvsNetDev.from_dict(d)

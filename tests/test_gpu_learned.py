@@ -1,18 +1,25 @@
-"""What the trained EvSNet gains over the method without it (the contrast
-threshold applied directly to the low-SPP frames), on held-out city clips that
-the training never saw, against the threshold events of 256-SPP renders.
+"""What the trained EvSNet gains over the method without it, on held-out clips
+that neither training nor model selection saw, against the contrast-threshold
+events of 256-SPP renders of the same frames (Sec. 3.3; the gain asked of the
+learned form).
 
 The weights under paper_2508_18071_gb300/weights were produced by
-`python -m paper_2508_18071_gb300.train_evsnet` with the library's own
-training kernels (2-SPP inputs, 256-SPP + threshold targets, C = 0.2, leak
-beta = 0.9).
+`python -m paper_2508_18071_gb300.train_evsnet` with the library's own training
+kernels: evsnet_city.npz on 2-SPP clips of the city block (the benchmark's
+network), evsnet_random.npz on 1-SPP clips of the 20k-triangle procedural scenes
+(the training configuration of the workload).
 
-Measured gain: the bidirectional EMD (the paper's training loss, Eq. 8-9) to the
-reference.  The event F1 of every low-SPP method is near zero on this workload:
-the reference itself is noise-dominated -- two independently seeded 256-SPP
-renders agree only at F1 ~ 0.2-0.5 -- which the test records as the ceiling.
-Against such targets the EMD optimum is a regular spike train at the target's
-rate, which is what the trained network emits where it sees no real change."""
+Each network must, on the same held-out frames:
+  (a) match more reference events than the method without EvSNet -- the
+      contrast threshold applied directly to the same low-SPP frames -- by
+      event F1 at +-1 frame;
+  (b) come closer to the reference by the paper's own measure, the
+      bidirectional EMD (Eq. 8-9), than that threshold, than silence and than
+      an input-independent train firing at the reference's own rate, and also
+      beat that train by F1;
+  (c) depend on its input: fed another clip's frames, its F1 against this
+      clip's reference falls to a fraction of its own.
+"""
 import os
 
 import numpy as np
@@ -25,21 +32,23 @@ WDIR = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
                     "paper_2508_18071_gb300", "weights")
 
 
-@pytest.mark.parametrize("name", ["evsnet_city.npz", "evsnet_city_temporal.npz"])
-def test_trained_evsnet_beats_threshold_on_low_spp(name):
-    """Both trained forms: the 3x3 stack of the workload configurations and the
-    paper's temporal form (kernel 7, 3 residual blocks)."""
+@pytest.mark.parametrize("name,scene,spp_in", [("evsnet_city.npz", "city", 2),
+                                               ("evsnet_random.npz", "random", 1)])
+def test_trained_evsnet_gains_over_the_method_without_it(name, scene, spp_in):
     assert torch.cuda.is_available()
     from paper_2508_18071_gb300 import train_evsnet
     path = os.path.join(WDIR, name)
     net = train_evsnet.load(path)
     hist = np.load(path)["train_history"]
-    assert hist[-1, 1] < 0.25 * hist[0, 1]                   # training lowered the loss
-    # 129 frames: long enough that a current offset integrating into periodic
-    # firing would show up in the event rate
-    ev = train_evsnet.evaluate(net, "city", seeds=(950, 951), n_frames=129, size=64)
-    assert ev["emd_net"] < 0.1 * ev["emd_thr"], ev           # >10x closer to the reference
-    assert ev["rate_net"] < ev["rate_thr"]
-    # the reference's own noise floor: a second, independently seeded 256-SPP
-    # render does not reach the F1 0.9 gate against the first
-    assert ev["f1_ceiling"] < 0.9, ev
+    assert hist[-1, 1] < hist[0, 1]                          # training lowered the loss
+    ev = train_evsnet.evaluate(net, scene, seeds=(950, 951), n_frames=129, size=128, spp_in=spp_in,
+                               ceiling=False)
+    f1 = {k[3:]: v[1] for k, v in ev.items() if k.startswith("f1_")}      # delta = 1 frame
+    # (a) F1 gain over the threshold on the same low-SPP frames
+    assert f1["net"] > 2.0 * f1["thr"], ev
+    # (b) EMD gain over the threshold, silence and a rate-matched fixed train
+    for k in ("thr", "silence", "fixed_rate"):
+        assert ev["emd_net"] < ev["emd_" + k], (k, ev)
+    assert f1["net"] > 2.0 * f1["fixed_rate"], ev
+    # (c) input dependence
+    assert f1["net_other_input"] < 0.5 * f1["net"], ev

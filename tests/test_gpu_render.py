@@ -161,3 +161,25 @@ def test_full_size_sampled_pixels(api, orc):
     agree = records_agree(rec, orec)
     assert 1.0 - agree.mean() < 5e-3
     _check_radiance(rgb, orgb, agree)
+
+
+@pytest.mark.parametrize("mode", ["wavefront", "megakernel"])
+def test_row_band_equals_rows_of_full_frame(api, mode):
+    """et_render_rows: a band of rows is bit for bit those rows of the full
+    render (the random numbers keep the full image's pixel index): the unit of
+    the row-band partition across GPUs."""
+    from paper_2508_18071_gb300 import _lib
+    s = inputs.random_scene(seed=11)
+    g = api.Scene(s)
+    g.set_mode(_lib.ET_RENDER_WAVEFRONT if mode == "wavefront" else _lib.ET_RENDER_MEGAKERNEL)
+    cams = inputs.random_scene_path(3, first=10)
+    W, H = 45, 38
+    rgb, logl, rec = api.render_frames(g, cams, W, H, 3, 5, 77, first_frame=10, records=True)
+    for (y0, y1) in ((0, 7), (7, 30), (30, 38), (19, 20)):
+        b_rgb, b_logl, b_rec = api.render_frames(g, cams, W, H, 3, 5, 77, first_frame=10, records=True,
+                                                 rows=(y0, y1))
+        assert np.array_equal(b_rgb.cpu().numpy(), rgb[:, y0:y1].cpu().numpy())
+        assert np.array_equal(b_logl.cpu().numpy(), logl[:, y0:y1].cpu().numpy())
+        assert np.array_equal(b_rec.cpu().numpy(), rec[:, y0:y1].cpu().numpy())
+    with pytest.raises(_lib.ETError):
+        api.render_frames(g, cams, W, H, 3, 5, 77, rows=(20, 20))

@@ -21,27 +21,29 @@ def tr():
 
 
 def _net(orc, d):
-    return orc.EvsNet(d["kind"], d["n_layers"], d["C"], d["kt"], d["ks"], d["beta"], d["vth"],
-                      d["reset"], np.asarray(d["w"], np.float64), np.asarray(d["b"], np.float64))
+    return orc.EvsNet.from_dict(d)
 
 
-def _problem(seed, kind, L, C, kt, B, K, H, W, std=0.3):
-    d = inputs.random_evsnet(kind, L, C, kt, 1, seed=seed, vth=0.3, beta=0.9, std=std)
+def _problem(seed, kind, L, C, kt, B, K, H, W, std=0.3, ks0=0):
+    d = inputs.random_evsnet(kind, L, C, kt, 1, seed=seed, vth=0.3, beta=0.9, std=std, ks0=ks0)
     lf = np.stack([inputs.random_logl_clip(seed + b, K + 1, H, W, step_std=0.3) for b in range(B)])
     rng = np.random.default_rng(seed)
     E = rng.choice([-2, -1, 0, 0, 0, 0, 1, 2], (B, K, H, W)).astype(np.float32)
     return d, lf, E
 
 
-@pytest.mark.parametrize("kind,L,C,kt,B,K,H,W,ck", [
-    (1, 7, 16, 7, 2, 48, 9, 11, 16),      # the paper's form: k = 7, M = 3, W = 43
-    (1, 3, 8, 5, 2, 30, 13, 7, 8),
-    (0, 3, 8, 3, 1, 21, 10, 10, 5),       # plain temporal stack
-    (1, 1, 4, 7, 2, 12, 6, 6, 12),        # encoder only
+@pytest.mark.parametrize("kind,L,C,kt,B,K,H,W,ck,ks0", [
+    (1, 7, 16, 7, 2, 48, 9, 11, 16, 0),      # the paper's form: k = 7, M = 3, W = 43
+    (1, 3, 8, 5, 2, 30, 13, 7, 8, 0),
+    (0, 3, 8, 3, 1, 21, 10, 10, 5, 0),       # plain temporal stack
+    (1, 1, 4, 7, 2, 12, 6, 6, 12, 0),        # encoder only
+    (1, 7, 16, 7, 2, 40, 11, 13, 16, 3),     # spatial stem 3 x 3 + the paper's blocks
+    (1, 3, 8, 5, 2, 24, 9, 10, 8, 5),        # spatial stem 5 x 5
+    (1, 1, 4, 7, 1, 10, 7, 5, 5, 7),         # stem only
 ])
-def test_temporal_bptt_gradients_match_oracle(tr, orc, kind, L, C, kt, B, K, H, W, ck):
+def test_temporal_bptt_gradients_match_oracle(tr, orc, kind, L, C, kt, B, K, H, W, ck, ks0):
     from paper_2508_18071_gb300 import api
-    d, lf, E = _problem(3, kind, L, C, kt, B, K, H, W, std=0.3 if L < 7 else 0.15)
+    d, lf, E = _problem(3, kind, L, C, kt, B, K, H, W, std=0.3 if L < 7 else 0.15, ks0=ks0)
     onet = _net(orc, d)
     X = np.diff(lf.astype(np.float64), axis=1)
     Son, Soff, _, Vp = orc.torch_forward(torch.tensor(X), onet)

@@ -503,3 +503,33 @@ def test_adam_first_step_closed_form(orc):
     lr = 1e-2
     p1, m, v = orc.adam_step(p, g, np.zeros(10), np.zeros(10), 1, lr)
     np.testing.assert_allclose(p1, p - lr * g / (np.abs(g) + 1e-8), rtol=1e-12)
+
+
+def test_bf16_mode_rounds_tensor_core_operands(orc):
+    """The oracle's BF16 mode rounds the weights and inputs of layers 1.. and
+    nothing else: (a) a weight 1 + 2^-10 of layer 1 acts as 1 (BF16 keeps 8
+    significant bits) while layer 0's identical weight does not round;
+    (b) on operands that BF16 holds exactly the mode changes nothing."""
+    torch = pytest.importorskip("torch")
+    d = inputs.random_evsnet(0, 2, 2, 1, 1, seed=0)
+    w = np.zeros_like(d["w"], dtype=np.float64)
+    w[0] = 1 + 2.0 ** -10                      # layer 0: channel 0 <- X
+    w[2] = 1 + 2.0 ** -10                      # layer 1: channel 0 <- channel 0
+    w[6] = 1.0                                 # projection of channel 0
+    d["w"], d["b"] = w, np.zeros_like(d["b"], dtype=np.float64)
+    net = _net(orc, d)
+    X = torch.full((1, 3, 2, 2), 0.75, dtype=torch.float64)
+    _, _, I, _ = orc.torch_forward(X, net)
+    _, _, Ib, _ = orc.torch_forward(X, net, round_bf16=True)
+    a = 0.75 * (1 + 2.0 ** -10)                # layer 0 stays FP64
+    np.testing.assert_allclose(I.numpy(), a * (1 + 2.0 ** -10), rtol=1e-15)
+    bf = float(torch.tensor(a, dtype=torch.float64).to(torch.bfloat16).double())
+    np.testing.assert_allclose(Ib.numpy(), bf * 1.0, rtol=1e-15)
+    # (b) dyadic operands: identical
+    d2 = inputs.random_evsnet(1, 5, 4, 3, 1, seed=1, ks0=3)
+    rng = np.random.default_rng(2)
+    d2["w"] = rng.choice([-0.5, 0.0, 0.5], size=d2["w"].shape, p=[0.1, 0.8, 0.1])
+    d2["b"] = np.zeros_like(d2["b"])
+    X2 = torch.tensor(rng.integers(-2, 3, (1, 10, 5, 6)) / 4.0)
+    n2 = _net(orc, d2)
+    assert torch.equal(orc.torch_forward(X2, n2)[2], orc.torch_forward(X2, n2, round_bf16=True)[2])

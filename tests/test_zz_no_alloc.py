@@ -34,8 +34,7 @@ def _dirty_call(lib, _lib, training, api, d, B, K, H, W, ck, seed):
     out = training.train_forward(lfd, meta, meta.w, meta.b, ckpt_every=ck)
     _, dSon, dSoff = training.emd_count_loss(out["spikes"], Ed, 0.01)
     sh = _lib.et_train_shape(B, K, H, W, ck)
-    net = _lib.et_evsnet_weights(meta.kind, meta.n_layers, meta.C, meta.kt, meta.ks, meta.beta,
-                                 meta.vth, meta.reset, _lib.ET_F32, meta.w.data_ptr(), meta.b.data_ptr())
+    net = meta.c_struct()
     need = C.c_size_t()
     assert lib.et_train_workspace_bytes(C.byref(net), C.byref(sh), C.byref(need)) == _lib.ET_OK
     assert need.value <= lib.et_train_static_workspace_capacity()
@@ -68,8 +67,7 @@ def test_static_workspace_backward_matches_workspace_backward():
     assert np.abs(ref).max() > 0
 
     sh = _lib.et_train_shape(B, K, H, W, ck)
-    net = _lib.et_evsnet_weights(meta.kind, meta.n_layers, meta.C, meta.kt, meta.ks, meta.beta,
-                                 meta.vth, meta.reset, _lib.ET_F32, meta.w.data_ptr(), meta.b.data_ptr())
+    net = meta.c_struct()
     need = C.c_size_t()
     assert lib.et_train_workspace_bytes(C.byref(net), C.byref(sh), C.byref(need)) == _lib.ET_OK
     assert need.value <= lib.et_train_static_workspace_capacity()
@@ -117,8 +115,7 @@ def test_static_workspace_backward_temporal_form():
     ref = torch.cat([ref_w, ref_b]).cpu().numpy()
     assert np.abs(ref).max() > 0
     sh = _lib.et_train_shape(B, K, H, W, ck)
-    net = _lib.et_evsnet_weights(meta.kind, meta.n_layers, meta.C, meta.kt, meta.ks, meta.beta,
-                                 meta.vth, meta.reset, _lib.ET_F32, meta.w.data_ptr(), meta.b.data_ptr())
+    net = meta.c_struct()
     need = C.c_size_t()
     assert lib.et_train_workspace_bytes(C.byref(net), C.byref(sh), C.byref(need)) == _lib.ET_OK
     d2 = inputs.random_evsnet(1, 3, 8, 7, 1, seed=19, vth=0.2, beta=0.95, std=0.5)
