@@ -55,24 +55,37 @@ struct TctParams {
 
 __device__ __forceinline__ int ring_pos(int s, int R) { return ((s % R) + R) % R; }
 
-// one pixel's 16 channels, BF16-rounded, as row `m` of a ring slot
-__device__ __forceinline__ void store_row(unsigned char* slot, int m, const float* v) {
-  __align__(16) __nv_bfloat162 h[CP / 2];
-#pragma unroll
-  for (int c = 0; c < CP / 2; ++c) h[c] = __floats2bfloat162_rn(v[2 * c], v[2 * c + 1]);
-  *reinterpret_cast<uint4*>(slot + m * 16) = reinterpret_cast<const uint4*>(h)[0];
-  *reinterpret_cast<uint4*>(slot + kPlane + m * 16) = reinterpret_cast<const uint4*>(h)[1];
+// two floats as one 32-bit word of BF16 (round to nearest even), low half first
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<const uint32_t*>(&h);
 }
 
-__device__ __forceinline__ void load_row(const unsigned char* slot, int m, float* v) {
-  __align__(16) __nv_bfloat162 h[CP / 2];
-  reinterpret_cast<uint4*>(h)[0] = *reinterpret_cast<const uint4*>(slot + m * 16);
-  reinterpret_cast<uint4*>(h)[1] = *reinterpret_cast<const uint4*>(slot + kPlane + m * 16);
+__device__ __forceinline__ float2 unpack_bf16(uint32_t w) {
+  __nv_bfloat162 h;
+  *reinterpret_cast<uint32_t*>(&h) = w;
+  return __bfloat1622float2(h);
+}
+
+// one pixel's 16 channels, BF16-rounded, as row `m` of a ring slot (channels
+// 0-7 in the first plane, 8-15 in the second)
+__device__ __forceinline__ void store_row(unsigned char* slot, int m, const float (&v)[CP]) {
+  *reinterpret_cast<uint4*>(slot + m * 16) =
+      make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
+  *reinterpret_cast<uint4*>(slot + kPlane + m * 16) =
+      make_uint4(pack_bf16(v[8], v[9]), pack_bf16(v[10], v[11]), pack_bf16(v[12], v[13]),
+                 pack_bf16(v[14], v[15]));
+}
+
+__device__ __forceinline__ void load_row(const unsigned char* slot, int m, float (&v)[CP]) {
+  const uint4 a = *reinterpret_cast<const uint4*>(slot + m * 16);
+  const uint4 b = *reinterpret_cast<const uint4*>(slot + kPlane + m * 16);
+  const uint32_t w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
 #pragma unroll
-  for (int c = 0; c < CP / 2; ++c) {
-    const float2 f = __bfloat1622float2(h[c]);
-    v[2 * c] = f.x;
-    v[2 * c + 1] = f.y;
+  for (int i = 0; i < 8; ++i) {
+    const float2 f = unpack_bf16(w[i]);
+    v[2 * i] = f.x;
+    v[2 * i + 1] = f.y;
   }
 }
 
@@ -147,9 +160,30 @@ evsnet_tct_kernel(TctParams P, const float* __restrict__ logl, const float* __re
   const uint32_t tmem = tmem_slot;
   const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
   const uint32_t idesc = umma_idesc_bf16(TP, CP);
+  const uint64_t a_desc0 = umma_desc(smem_u32(rings), kPlane, 128);
+  const uint64_t b_desc0 = umma_desc(smem_u32(wB), CP * 16, 128);
   uint32_t phase = 0;
 
   const int S = P.F - P.f0;             // steps of this call
+  // 3 x 3 stem: the nine neighbours' X of the steps of a chunk, loaded one
+  // chunk ahead so that their latency hides behind the tensor-core layers
+  float xn[kT][9];
+  auto load_x9 = [&](int s_first) {
+#pragma unroll
+    for (int j = 0; j < kT; ++j) {
+      const int f = P.f0 + s_first + j;
+#pragma unroll
+      for (int t = 0; t < 9; ++t) {
+        const int yy = py + t / 3 - 1, xx = px + t % 3 - 1;
+        const bool in = live && s_first + j < S && yy >= 0 && yy < P.H && xx >= 0 && xx < P.W;
+        const int64_t qq = in ? (int64_t)yy * P.W + xx : 0;
+        const float xc = in ? __ldg(logl + (int64_t)f * npix + qq) : 0.0f;
+        const float xp = !in ? 0.0f : (f == 0 ? last_l[qq] : __ldg(logl + (int64_t)(f - 1) * npix + qq));
+        xn[j][t] = xc - xp;
+      }
+    }
+  };
+  if (ks0 == 3) load_x9(0);
   for (int s0 = 0; s0 < S && !bail; s0 += kT) {
     const int tc = min(kT, S - s0);
     float h[kT][CP];                    // block input (residual) / current activation, FP32
@@ -162,7 +196,15 @@ evsnet_tct_kernel(TctParams P, const float* __restrict__ logl, const float* __re
 #pragma unroll
       for (int c = 0; c < CP; ++c) acc[c] = bs[c];
       if (live) {
-        if (ks0 > 0) {
+        if (ks0 == 3) {
+          // the 3 x 3 stem on the neighbours' X loaded during the previous chunk
+#pragma unroll
+          for (int t = 0; t < 9; ++t) {
+            const float* wt = w0 + t * CP;
+#pragma unroll
+            for (int c = 0; c < CP; ++c) acc[c] = fmaf(wt[c], xn[j][t], acc[c]);
+          }
+        } else if (ks0 > 0) {
           const int r0 = ks0 >> 1;
           for (int dy = 0; dy < ks0; ++dy) {
             const int yy = py + dy - r0;
@@ -195,6 +237,7 @@ evsnet_tct_kernel(TctParams P, const float* __restrict__ logl, const float* __re
       for (int c = 0; c < CP; ++c) h[j][c] = live ? fmaxf(acc[c], 0.0f) : 0.0f;
       store_row(slot_of(1, ring_pos(s0 + j, R)), tid, h[j]);
     }
+    if (ks0 == 3) load_x9(s0 + kT);   // next chunk's inputs, consumed after these layers
     // ---- layers 1 .. L-1 on the tensor core
     for (int l = 1; l < L; ++l) {
       fence_proxy_async_smem();
@@ -202,12 +245,17 @@ evsnet_tct_kernel(TctParams P, const float* __restrict__ logl, const float* __re
       __syncthreads();
       tc_fence_after();
       if (tid == 0) {
-        const uint32_t bbase = smem_u32(wB + (size_t)(l - 1) * kt * (CP * CP * 2));
+        // descriptors differ only in their start-address field (16-byte units):
+        // slots are 4 KB apart, B blocks 512 B
+        const uint64_t a0 = a_desc0 + (uint64_t)((l - 1) * R) * (kSlot >> 4);
+        const uint64_t b0 = b_desc0 + (uint64_t)((l - 1) * kt) * ((CP * CP * 2) >> 4);
+        const int p0 = ring_pos(s0 - hk, R);
         for (int j = 0; j < tc; ++j)
           for (int tau = 0; tau < kt; ++tau) {
-            const uint64_t ad = umma_desc(smem_u32(slot_of(l, ring_pos(s0 + j - hk + tau, R))), kPlane, 128);
-            const uint64_t bd = umma_desc(bbase + tau * (CP * CP * 2), CP * 16, 128);
-            umma_bf16(tmem + j * CP, ad, bd, idesc, tau != 0);
+            int pos = p0 + j + tau;
+            pos = pos >= R ? pos - R : pos;
+            umma_bf16(tmem + j * CP, a0 + (uint64_t)pos * (kSlot >> 4),
+                      b0 + (uint64_t)tau * ((CP * CP * 2) >> 4), idesc, tau != 0);
           }
         umma_commit(&mma_bar);
       }

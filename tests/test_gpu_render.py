@@ -14,8 +14,12 @@ hit point whose FP32 position error (~1e-7 m) is a sizeable fraction of the
 under 1e-6 absolute (their radiance is ~1e-4).  A glossy GGX lobe of roughness
 alpha = 0.05 amplifies direction rounding by d ln D / d theta ~ 4 / alpha^2
 ~ 1600, i.e. 6e-8 -> 1e-4 relative per glossy bounce.  So every agreeing pixel
-must be within 2e-3 |ref| + 1e-6, and at least 99.9 % of them within the strict
-1e-4 |ref| + 1e-7."""
+must be within the strict 1e-4 |ref| + 1e-7 unless the oracle's conditioning
+record says one of its paths met such a case -- a light connection or emitter
+hit with light-side or surface-side cosine below COS_ILL, or a GGX shading
+point of roughness below ALPHA_ILL -- and those pixels within 2e-3 |ref| + 1e-6.
+Any other pixel outside the strict bar fails.  Path records may disagree on at
+most 0.1 % of the pixels (measured: 0 to 0.024 % on these scenes)."""
 
 import numpy as np
 import pytest
@@ -28,16 +32,26 @@ pytestmark = pytest.mark.gpu
 RTOL, ATOL = 1e-4, 1e-7
 ATOL_GRAZING = 1e-6
 RTOL_ILL = 2e-3
-STRICT_FRAC = 0.999
+COS_ILL = 0.02
+ALPHA_ILL = 0.1
+MAX_DISAGREE = 1e-3
 
 
-def _check_radiance(rgb, orgb, agree):
+def ill_conditioned(cond):
+    """[F,H,W] mask from the oracle's conditioning record [F,H,W,3]."""
+    return (cond[..., 0] < COS_ILL) | (cond[..., 1] < COS_ILL) | (cond[..., 2] < ALPHA_ILL)
+
+
+def _check_radiance(rgb, orgb, agree, cond):
     loose = rel_close(rgb, orgb, RTOL_ILL, ATOL_GRAZING).all(-1)
     strict = rel_close(rgb, orgb, RTOL, ATOL).all(-1)
+    ill = ill_conditioned(cond)
+    bad = np.argwhere(agree & ~strict & ~ill)
+    assert len(bad) == 0, [(tuple(i), rgb[tuple(i)].tolist(), orgb[tuple(i)].tolist(),
+                            cond[tuple(i)].tolist()) for i in bad[:5]]
     bad = np.argwhere(agree & ~loose)
     assert len(bad) == 0, [(tuple(i), rgb[tuple(i)].tolist(), orgb[tuple(i)].tolist())
                            for i in bad[:5]]
-    assert strict[agree].mean() >= STRICT_FRAC, strict[agree].mean()
 
 
 @pytest.fixture(scope="module")
@@ -52,17 +66,17 @@ def _oscene(orc, s):
     return orc.Scene(s["tris"], s["tri_mat"], s["materials"], s["lights"], s["env"])
 
 
-def _compare(api, orc, s, cams, W, H, spp, depth, seed, first=0, max_bad=1e-3):
+def _compare(api, orc, s, cams, W, H, spp, depth, seed, first=0, max_bad=MAX_DISAGREE):
     g = api.Scene(s)
     rgb, logl, rec = api.render_frames(g, cams, W, H, spp, depth, seed, first_frame=first,
                                        records=True)
     rgb, logl, rec = rgb.cpu().numpy(), logl.cpu().numpy(), rec.cpu().numpy()
     o = _oscene(orc, s)
-    orgb, orec = o.render(cams, W, H, spp, depth, seed, first_frame=first, records=True)
+    orgb, orec, cond = o.render(cams, W, H, spp, depth, seed, first_frame=first, records=True, cond=True)
     agree = records_agree(rec, orec)
     bad_frac = 1.0 - agree.mean()
     assert bad_frac < max_bad, bad_frac
-    _check_radiance(rgb, orgb, agree)
+    _check_radiance(rgb, orgb, agree, cond)
     # Eq. 1 prologue from the GPU's own radiance: luminance and ln(L + 1e-3)
     L = (rgb.astype(np.float64) @ np.array([0.2126, 0.7152, 0.0722]))
     np.testing.assert_allclose(logl, np.log(L + 1e-3), rtol=1e-6, atol=1e-6)
@@ -84,7 +98,7 @@ def test_random_scene_ggx_ragged(api, orc):
     5, a ragged 37 x 23 image (partial tiles)."""
     s = inputs.random_scene(seed=11)
     cams = inputs.random_scene_path(2, first=50)
-    _compare(api, orc, s, cams, 37, 23, 4, 5, seed=12345678901, first=50, max_bad=5e-3)
+    _compare(api, orc, s, cams, 37, 23, 4, 5, seed=12345678901, first=50)
 
 
 def test_white_furnace(api):
@@ -156,11 +170,12 @@ def test_full_size_sampled_pixels(api, orc):
     rgb = rgb[:, rows[0]:rows[1]].cpu().numpy()
     rec = rec[:, rows[0]:rows[1]].cpu().numpy()
     o = _oscene(orc, s)
-    orgb, orec = o.render(cams, 1280, 720, 2, 5, 0, first_frame=500, rows=rows, records=True)
-    orgb, orec = orgb[:, rows[0]:rows[1]], orec[:, rows[0]:rows[1]]
+    orgb, orec, cond = o.render(cams, 1280, 720, 2, 5, 0, first_frame=500, rows=rows, records=True,
+                                cond=True)
+    orgb, orec, cond = orgb[:, rows[0]:rows[1]], orec[:, rows[0]:rows[1]], cond[:, rows[0]:rows[1]]
     agree = records_agree(rec, orec)
-    assert 1.0 - agree.mean() < 5e-3
-    _check_radiance(rgb, orgb, agree)
+    assert 1.0 - agree.mean() < MAX_DISAGREE
+    _check_radiance(rgb, orgb, agree, cond)
 
 
 @pytest.mark.parametrize("mode", ["wavefront", "megakernel"])
