@@ -53,7 +53,7 @@ def parse():
     p.add_argument("--cpu-frames", type=int, default=2, help="oracle sample: frames")
     p.add_argument("--evsnet-dtype", default="auto", choices=["auto", "f32", "bf16", "fp8"],
                    help="auto: BF16 where the network's form has a tensor-core kernel, else FP32")
-    p.add_argument("--bvh", default=None, choices=["gpu", "host", "sweep"],
+    p.add_argument("--bvh", default=None, choices=["gpu_sweep", "gpu", "host", "sweep"],
                    help="hierarchy builder (default: the library's)")
     p.add_argument("--no-sweep", action="store_true",
                    help="skip the EvSNet precision sweep (FP32 / BF16 / FP8) after the timed region")
@@ -781,6 +781,7 @@ def main():
         hbm = peaks.get("hbm_gbs") or 6800.0
         hbm_src = "MEASURED_PEAKS hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback 6.8 TB/s"
         l2 = l2_copy_gbs(dev)
+        l1_peak = props.multi_processor_count * 128 * 2.07e9 / 1e9
         fp32_peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * 2.07e9 / 1e12
         fp32_src = ("derived, not measured: %d SMs x 128 FP32 lanes x 2 x 2.07 GHz (unit counts and "
                     "maximum clock; the measured peaks hold no FP32 figure)" % props.multi_processor_count)
@@ -795,11 +796,16 @@ def main():
                         "peak": fp32_peak, "unit": "TFLOP/s",
                         "frac": work["flops_per_ray"] * rays / t_tr / 1e12 / fp32_peak,
                         "peak_source": fp32_src},
-                "l2": {"bound": "l2", "achieved": work["bytes_per_ray"] * rays / t_tr / 1e9, "peak": l2,
-                       "unit": "GB/s", "frac": work["bytes_per_ray"] * rays / t_tr / 1e9 / l2,
-                       "peak_source": "measured here: device copy of 24 MB within L2 (read + write)",
+                "l1": {"bound": "l1", "achieved": work["bytes_per_ray"] * rays / t_tr / 1e9, "peak": l1_peak,
+                       "unit": "GB/s", "frac": work["bytes_per_ray"] * rays / t_tr / 1e9 / l1_peak,
+                       "peak_source": "derived, not measured: %d SMs x 128 B per clock x 2.07 GHz"
+                                      % props.multi_processor_count,
                        "work": "64 B per node visit + 36 B per triangle test (%.0f B/ray, full-sweep "
-                               "SAH counts)" % work["bytes_per_ray"]}}
+                               "SAH counts)" % work["bytes_per_ray"],
+                       "note": "the node and triangle fetches hit in L1 (89 %% of sectors in ncu on "
+                               "320x180); measured there: L1 8.2, L2 3.7, DRAM 0.14 TB/s during "
+                               "wf_trace (profiles/wf_trace_bytes_city320x180.md); L2 copy here: "
+                               "%.0f GB/s" % l2}}
             # bytes each kernel reads and writes per item, from the queue records
             # (wavefront state: rays 32 B, path state 16 + 16 B, hits 8 B, shadow
             # rays 48 B, triangles 48 B)

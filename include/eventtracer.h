@@ -88,14 +88,18 @@ int et_build_scene(const float* tris, const uint32_t* tri_mat, int64_t n_tris,
                    et_scene** out, void* stream);
 /* Hierarchy builders, all minimising the SAH cost C = 1 + (A_L N_L + A_R N_R) / A
  * per split (leaf cost N):
- *   ET_BVH_GPU    32 centroid bins per axis, on the device, level by level (fast);
- *   ET_BVH_HOST   the same binned heuristic on the host;
- *   ET_BVH_SWEEP  every split of the centroid order on each axis, on the host
- *                 (O(n log n); slower to build, fewer traversal steps).
+ *   ET_BVH_GPU_SWEEP  every split of the centroid order on each axis, on the
+ *                     device, level by level (the default: the host sweep's
+ *                     tree and node order, built on the GPU);
+ *   ET_BVH_GPU        32 centroid bins per axis, on the device, level by level;
+ *   ET_BVH_HOST       the same binned heuristic on the host;
+ *   ET_BVH_SWEEP      every split of the centroid order on each axis, on the host
+ *                     (O(n log n); the full sweep's trees need fewer traversal
+ *                     steps than the binned ones).
  * A requested build whose tree is deeper than the traversal stack's 64 levels
  * (or a GPU build that fails) is replaced by the host binned build. */
-enum { ET_BVH_GPU = 0, ET_BVH_HOST = 1, ET_BVH_SWEEP = 2 };
-#define ET_BVH_DEFAULT ET_BVH_SWEEP
+enum { ET_BVH_GPU = 0, ET_BVH_HOST = 1, ET_BVH_SWEEP = 2, ET_BVH_GPU_SWEEP = 3 };
+#define ET_BVH_DEFAULT ET_BVH_GPU_SWEEP
 /* et_build_scene with an explicit builder.  Errors as et_build_scene, and
  * ET_ERR_ARG for an unknown builder. */
 int et_build_scene_with(const float* tris, const uint32_t* tri_mat, int64_t n_tris,
@@ -173,14 +177,17 @@ int et_render_annotations(const et_scene* scene, const et_camera* cams, int32_t 
                           float* normal, int32_t* prim, int32_t* material, float* flow,
                           void* stream);
 
-/* Schedule used by et_render_frames on this scene; both compute identical
- * outputs.  ET_RENDER_WAVEFRONT (default): paths advance one segment at a time
+/* Schedule used by et_render_frames on this scene; all compute identical
+ * outputs.  ET_RENDER_WAVEFRONT: paths advance one segment at a time
  * through compacted ray queues traced by persistent warps that refill idle
  * lanes; it keeps a device workspace in the scene (up to ~1.3 GB for 8M paths
  * in flight), allocated by the first call that needs it and kept until
  * et_scene_free.  ET_RENDER_MEGAKERNEL: one thread per pixel, no workspace.
+ * ET_RENDER_WAVEFRONT_TILES (default): the wavefront schedule with each warp's
+ * primary rays taken from an 8 x 4 pixel tile instead of 32 pixels of one row
+ * (when W is a multiple of 8 and the rendered rows of 4; else raster order).
  * Errors: ET_ERR_ARG. */
-enum { ET_RENDER_WAVEFRONT = 0, ET_RENDER_MEGAKERNEL = 1 };
+enum { ET_RENDER_WAVEFRONT = 0, ET_RENDER_MEGAKERNEL = 1, ET_RENDER_WAVEFRONT_TILES = 2 };
 int et_render_set_mode(et_scene* scene, int32_t mode);
 
 /* Per-kernel device time of the wavefront schedule, for measurement (not part

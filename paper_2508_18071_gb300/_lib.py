@@ -15,8 +15,8 @@ ET_LAMBERT, ET_GGX = 0, 1
 ET_LOG_EPS, ET_LOG_PAPER = 0, 1
 ET_F32, ET_BF16, ET_FP8 = 0, 1, 2
 ET_NET_STACK, ET_NET_RESIDUAL = 0, 1
-ET_RENDER_WAVEFRONT, ET_RENDER_MEGAKERNEL = 0, 1
-ET_BVH_GPU, ET_BVH_HOST, ET_BVH_SWEEP = 0, 1, 2
+ET_RENDER_WAVEFRONT, ET_RENDER_MEGAKERNEL, ET_RENDER_WAVEFRONT_TILES = 0, 1, 2
+ET_BVH_GPU, ET_BVH_HOST, ET_BVH_SWEEP, ET_BVH_GPU_SWEEP = 0, 1, 2, 3
 
 
 class et_material(C.Structure):

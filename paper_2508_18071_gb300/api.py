@@ -32,9 +32,11 @@ def _ptr(t: Optional[torch.Tensor]):
 # ----------------------------------------------------------------------- scene
 class Scene:
     """et_build_scene: geometry + BVH on the device (see inputs.py for the dict layout).
-    builder: None (the library's default), "gpu", "host" or "sweep" (et_build_scene_with)."""
+    builder: None (the library's default, "gpu_sweep"), "gpu_sweep", "gpu", "host" or "sweep"
+    (et_build_scene_with)."""
 
-    BUILDERS = {"gpu": L.ET_BVH_GPU, "host": L.ET_BVH_HOST, "sweep": L.ET_BVH_SWEEP}
+    BUILDERS = {"gpu": L.ET_BVH_GPU, "host": L.ET_BVH_HOST, "sweep": L.ET_BVH_SWEEP,
+                "gpu_sweep": L.ET_BVH_GPU_SWEEP}
 
     def __init__(self, scene: dict, stream=None, builder=None):
         lib = L.load()
@@ -77,7 +79,7 @@ class Scene:
                                                              _stream(stream)))
 
     def set_mode(self, mode: int):
-        """ET_RENDER_WAVEFRONT (default) or ET_RENDER_MEGAKERNEL."""
+        """ET_RENDER_WAVEFRONT_TILES (default), ET_RENDER_WAVEFRONT or ET_RENDER_MEGAKERNEL."""
         L.check("et_render_set_mode", L.load().et_render_set_mode(self._h, int(mode)))
 
     PROFILE_KINDS = ("raygen", "trace", "shade", "shadow", "accumulate")

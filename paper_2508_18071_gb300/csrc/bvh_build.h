@@ -1,10 +1,11 @@
-// Host-side records shared by the two BVH builders (host C++ and GPU).
+// Host-side records shared by the BVH builders (host C++ and GPU).
 #pragma once
 #include <algorithm>
 #include <cfloat>
 #include <cstdint>
 #include <vector>
 #include <cuda_runtime.h>
+#include "et_internal.cuh"
 
 struct Box {
   float lo[3], hi[3];
@@ -28,6 +29,30 @@ struct BuildNode { Box box; int left, right, first, count; };
 
 constexpr int kSahBins = 32;
 constexpr int kLeafMax = 4;
+
+// Device buffer of the builders, grown on demand and freed with the builder.
+template <class T>
+struct DevBuf {
+  T* p = nullptr;
+  size_t cap = 0;
+  int ensure(size_t n) {
+    if (n <= cap) return ET_OK;
+    cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    ET_CHECK_CUDA(cudaMalloc(&p, sizeof(T) * std::max<size_t>(n, 1)));
+    cap = n;
+    return ET_OK;
+  }
+  ~DevBuf() { cudaFree(p); }
+};
+
+// GPU full-sweep SAH build (the host sweep's algorithm and node order):
+// node list (node 0 = root), the triangle permutation in leaf order and the
+// tree depth.  ET_ERR_UNIMPLEMENTED if the tree is deeper than the traversal
+// stack.
+int gpu_sweep_sah(const float* tris, int64_t n, cudaStream_t stream, std::vector<BuildNode>& nodes,
+                  std::vector<int>& perm, int& max_depth);
 
 // GPU binned-SAH build of n triangles (host array [n][9]): fills the node list
 // (node 0 = root), the triangle permutation in leaf order and the tree depth.

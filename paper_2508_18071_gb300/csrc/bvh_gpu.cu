@@ -233,21 +233,7 @@ task_partition(const int2* __restrict__ chunks, const Task* __restrict__ tasks, 
   }
 }
 
-template <class T>
-struct DevBuf {
-  T* p = nullptr;
-  size_t cap = 0;
-  int ensure(size_t n) {
-    if (n <= cap) return ET_OK;
-    cudaFree(p);
-    p = nullptr;
-    cap = 0;
-    ET_CHECK_CUDA(cudaMalloc(&p, sizeof(T) * std::max<size_t>(n, 1)));
-    cap = n;
-    return ET_OK;
-  }
-  ~DevBuf() { cudaFree(p); }
-};
+
 
 }  // namespace
 

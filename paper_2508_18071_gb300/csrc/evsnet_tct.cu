@@ -5,8 +5,11 @@
 // layers 1.. and their inputs), FP32 accumulation in TMEM; layer 0, the
 // residual sums, the projection and BiLIF stay FP32.
 //
-// A CTA owns a tile of 128 consecutive pixels for the whole call: one thread
-// per pixel, one TMEM lane per pixel.  The input history of every layer >= 1
+// A CTA owns a tile of 128 consecutive pixels for the whole call: one TMEM
+// lane per pixel and two threads per pixel (warps w and w + 4 share TMEM lane
+// quarter w), each owning 8 of the 16 channels -- its 8 accumulator columns,
+// one 16-byte plane row of the operands and half of every epilogue -- so that
+// two warps per scheduler hide each other's latencies.  The input history of every layer >= 1
 // (its last kt inputs) lives in shared memory as a ring of kt + kT - 1 slots,
 // each slot one step of 128 pixels x 16 channels in the K-major, no-swizzle
 // operand layout (two 2 KB planes of 8 channels, 16-byte rows), so the A
@@ -39,7 +42,8 @@ constexpr int kMaxKt = 7;
 constexpr int kMaxStem = 7;
 constexpr int kSlot = TP * CP * 2;      // bytes of one ring slot
 constexpr int kPlane = TP * 16;         // bytes of 8 channels of 128 rows
-constexpr int kThreads = TP;
+constexpr int kHalf = CP / 2;            // channels per thread
+constexpr int kThreads = 2 * TP;
 constexpr uint32_t kTmemCols = 32;      // kT x 16 accumulator columns
 constexpr unsigned long long kTimeoutBit = 1ull << 62;
 
@@ -67,22 +71,18 @@ __device__ __forceinline__ float2 unpack_bf16(uint32_t w) {
   return __bfloat1622float2(h);
 }
 
-// one pixel's 16 channels, BF16-rounded, as row `m` of a ring slot (channels
-// 0-7 in the first plane, 8-15 in the second)
-__device__ __forceinline__ void store_row(unsigned char* slot, int m, const float (&v)[CP]) {
-  *reinterpret_cast<uint4*>(slot + m * 16) =
+// 8 channels of one pixel, BF16-rounded, as row `m` of plane `hc` of a ring
+// slot (plane 0: channels 0-7, plane 1: channels 8-15)
+__device__ __forceinline__ void store_half(unsigned char* slot, int hc, int m, const float (&v)[kHalf]) {
+  *reinterpret_cast<uint4*>(slot + hc * kPlane + m * 16) =
       make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
-  *reinterpret_cast<uint4*>(slot + kPlane + m * 16) =
-      make_uint4(pack_bf16(v[8], v[9]), pack_bf16(v[10], v[11]), pack_bf16(v[12], v[13]),
-                 pack_bf16(v[14], v[15]));
 }
 
-__device__ __forceinline__ void load_row(const unsigned char* slot, int m, float (&v)[CP]) {
-  const uint4 a = *reinterpret_cast<const uint4*>(slot + m * 16);
-  const uint4 b = *reinterpret_cast<const uint4*>(slot + kPlane + m * 16);
-  const uint32_t w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+__device__ __forceinline__ void load_half(const unsigned char* slot, int hc, int m, float (&v)[kHalf]) {
+  const uint4 a = *reinterpret_cast<const uint4*>(slot + hc * kPlane + m * 16);
+  const uint32_t w[4] = {a.x, a.y, a.z, a.w};
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
+  for (int i = 0; i < 4; ++i) {
     const float2 f = unpack_bf16(w[i]);
     v[2 * i] = f.x;
     v[2 * i + 1] = f.y;
@@ -99,10 +99,14 @@ evsnet_tct_kernel(TctParams P, const float* __restrict__ logl, const float* __re
   __shared__ uint64_t mma_bar;
   __shared__ uint32_t tmem_slot;
   __shared__ int bail;
+  __shared__ float part[kT][TP];        // the second half's share of the projection
   const int L = P.L, C = P.C, kt = P.kt, R = P.R, hk = kt - 1, ks0 = P.ks0;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int p = tid & (TP - 1);         // pixel of the tile = TMEM lane
+  const int hc = tid >> 7;              // channel half: channels 8 hc .. 8 hc + 7
+  const int c0 = hc * kHalf;
   const int64_t npix = (int64_t)P.H * P.W;
-  const int64_t q = (int64_t)blockIdx.x * TP + tid;
+  const int64_t q = (int64_t)blockIdx.x * TP + p;
   const bool live = q < npix;
   const int px = live ? (int)(q % P.W) : 0, py = live ? (int)(q / P.W) : 0;
   unsigned char* rings = sm;                                   // [L-1][R] slots
@@ -139,26 +143,27 @@ evsnet_tct_kernel(TctParams P, const float* __restrict__ logl, const float* __re
                          (k & 7) * 2;
     *reinterpret_cast<__nv_bfloat16*>(dst) = __float2bfloat16_rn(v);
   }
-  // ring slots of steps -(kt-1) .. -1 from the state (oldest first); others zero
+  // ring slots of steps -(kt-1) .. -1 from the state (oldest first)
   for (int l = 1; l < L; ++l) {
     for (int j = 0; j < hk; ++j) {
-      float v[CP];
+      float v[kHalf];
 #pragma unroll
-      for (int c = 0; c < CP; ++c) v[c] = (live && c < C) ? hist[hidx(l, j, c)] : 0.0f;
-      store_row(slot_of(l, ring_pos(j - hk, R)), tid, v);
+      for (int c = 0; c < kHalf; ++c) v[c] = (live && c0 + c < C) ? hist[hidx(l, j, c0 + c)] : 0.0f;
+      store_half(slot_of(l, ring_pos(j - hk, R)), hc, p, v);
     }
   }
   if (ks0 == 0) {
-    for (int j = 0; j < hk; ++j) xh[ring_pos(j - hk, R) * TP + tid] = live ? hist[hidx(0, j, 0)] : 0.0f;
+    // both halves write the same values: each reads back its own writes
+    for (int j = 0; j < hk; ++j) xh[ring_pos(j - hk, R) * TP + p] = live ? hist[hidx(0, j, 0)] : 0.0f;
   }
-  float V = live ? Vg[q] : 0.0f;
+  float V = (live && hc == 0) ? Vg[q] : 0.0f;
   if (warp == 0) tmem_alloc(&tmem_slot, kTmemCols);
   if (tid == 0) { mbar_init(&mma_bar, 1); bail = 0; }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
-  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+  const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
   const uint32_t idesc = umma_idesc_bf16(TP, CP);
   const uint64_t a_desc0 = umma_desc(smem_u32(rings), kPlane, 128);
   const uint64_t b_desc0 = umma_desc(smem_u32(wB), CP * 16, 128);
@@ -186,23 +191,23 @@ evsnet_tct_kernel(TctParams P, const float* __restrict__ logl, const float* __re
   if (ks0 == 3) load_x9(0);
   for (int s0 = 0; s0 < S && !bail; s0 += kT) {
     const int tc = min(kT, S - s0);
-    float h[kT][CP];                    // block input (residual) / current activation, FP32
+    const int pc = ring_pos(s0, R);     // ring position of the chunk's first step
+    float h[kT][kHalf];                 // block input (residual) / current activation, FP32
     // ---- layer 0 on CUDA cores, FP32: X_k = l_k - l_{k-1} (Eq. 1)
 #pragma unroll
     for (int j = 0; j < kT; ++j) {
       if (j >= tc) break;
       const int f = P.f0 + s0 + j;
-      float acc[CP];
+      float acc[kHalf];
 #pragma unroll
-      for (int c = 0; c < CP; ++c) acc[c] = bs[c];
+      for (int c = 0; c < kHalf; ++c) acc[c] = bs[c0 + c];
       if (live) {
         if (ks0 == 3) {
-          // the 3 x 3 stem on the neighbours' X loaded during the previous chunk
 #pragma unroll
           for (int t = 0; t < 9; ++t) {
-            const float* wt = w0 + t * CP;
+            const float* wt = w0 + t * CP + c0;
 #pragma unroll
-            for (int c = 0; c < CP; ++c) acc[c] = fmaf(wt[c], xn[j][t], acc[c]);
+            for (int c = 0; c < kHalf; ++c) acc[c] = fmaf(wt[c], xn[j][t], acc[c]);
           }
         } else if (ks0 > 0) {
           const int r0 = ks0 >> 1;
@@ -216,26 +221,27 @@ evsnet_tct_kernel(TctParams P, const float* __restrict__ logl, const float* __re
               const float xc = __ldg(logl + (int64_t)f * npix + qq);
               const float xp = f == 0 ? last_l[qq] : __ldg(logl + (int64_t)(f - 1) * npix + qq);
               const float v = xc - xp;
-              const float* wt = w0 + (dy * ks0 + dx) * CP;
+              const float* wt = w0 + (dy * ks0 + dx) * CP + c0;
 #pragma unroll
-              for (int c = 0; c < CP; ++c) acc[c] = fmaf(wt[c], v, acc[c]);
+              for (int c = 0; c < kHalf; ++c) acc[c] = fmaf(wt[c], v, acc[c]);
             }
           }
         } else {
           const float xc = __ldg(logl + (int64_t)f * npix + q);
           const float xp = f == 0 ? last_l[q] : __ldg(logl + (int64_t)(f - 1) * npix + q);
-          xh[ring_pos(s0 + j, R) * TP + tid] = xc - xp;
+          xh[ring_pos(s0 + j, R) * TP + p] = xc - xp;
           for (int tau = 0; tau < kt; ++tau) {
-            const float v = xh[ring_pos(s0 + j - hk + tau, R) * TP + tid];
-            const float* wt = w0 + tau * CP;
+            const float v = xh[ring_pos(s0 + j - hk + tau, R) * TP + p];
+            const float* wt = w0 + tau * CP + c0;
 #pragma unroll
-            for (int c = 0; c < CP; ++c) acc[c] = fmaf(wt[c], v, acc[c]);
+            for (int c = 0; c < kHalf; ++c) acc[c] = fmaf(wt[c], v, acc[c]);
           }
         }
       }
 #pragma unroll
-      for (int c = 0; c < CP; ++c) h[j][c] = live ? fmaxf(acc[c], 0.0f) : 0.0f;
-      store_row(slot_of(1, ring_pos(s0 + j, R)), tid, h[j]);
+      for (int c = 0; c < kHalf; ++c) h[j][c] = live ? fmaxf(acc[c], 0.0f) : 0.0f;
+      const int pj = pc + j >= R ? pc + j - R : pc + j;
+      store_half(slot_of(1, pj), hc, p, h[j]);
     }
     if (ks0 == 3) load_x9(s0 + kT);   // next chunk's inputs, consumed after these layers
     // ---- layers 1 .. L-1 on the tensor core
@@ -273,46 +279,60 @@ evsnet_tct_kernel(TctParams P, const float* __restrict__ logl, const float* __re
 #pragma unroll
       for (int j = 0; j < kT; ++j) {
         if (j >= tc) break;
-        float acc[CP];
-        tmem_ld16(tmem + lane_base + j * CP, acc);
-        float out[CP];
+        float acc[kHalf];
+        tmem_ld8(tmem + lane_base + j * CP + c0, acc);
+        float out[kHalf];
 #pragma unroll
-        for (int c = 0; c < CP; ++c) {
-          const float v = acc[c] + bs[l * CP + c];
+        for (int c = 0; c < kHalf; ++c) {
+          const float v = acc[c] + bs[l * CP + c0 + c];
           if (closing) { h[j][c] = fmaxf(h[j][c] + v, 0.0f); out[c] = h[j][c]; }
           else if (inner) out[c] = fmaxf(v, 0.0f);
           else { out[c] = fmaxf(v, 0.0f); h[j][c] = out[c]; }
           if (!live) out[c] = 0.0f;
         }
-        if (l + 1 < L) store_row(slot_of(l + 1, ring_pos(s0 + j, R)), tid, out);
-        else {
+        if (l + 1 < L) {
+          const int pj = pc + j >= R ? pc + j - R : pc + j;
+          store_half(slot_of(l + 1, pj), hc, p, out);
+        } else {
 #pragma unroll
-          for (int c = 0; c < CP; ++c) h[j][c] = out[c];
+          for (int c = 0; c < kHalf; ++c) h[j][c] = out[c];
         }
       }
       tc_fence_before();
     }
     if (bail) break;
-    // ---- Eq. 6 projection and BiLIF, step by step
+    // ---- Eq. 6 projection (each half its 8 channels) and BiLIF, step by step
 #pragma unroll
     for (int j = 0; j < kT; ++j) {
       if (j >= tc) break;
-      const int f = P.f0 + s0 + j;
-      uint32_t nev = 0;
-      int Sp = 0;
-      if (live) {
-        float I = bp[0];
+      float Ih = hc == 0 ? bp[0] : 0.0f;
 #pragma unroll
-        for (int c = 0; c < CP; ++c) I = fmaf(wp[c], h[j][c], I);
-        const float vp = P.beta * V + I;
-        Sp = vp >= P.vth ? 1 : (vp <= -P.vth ? -1 : 0);
-        V = vp - P.reset * (float)Sp;
-        nev = (Sp != 0 && P.t0 + f >= 0) ? 1u : 0u;   // delayed labels below 0: none
-        const int64_t o = (int64_t)(s0 + j) * npix + q;
-        if (I_out) I_out[o] = I;
-        if (spikes) spikes[o] = (int8_t)Sp;
+      for (int c = 0; c < kHalf; ++c) Ih = fmaf(wp[c0 + c], h[j][c], Ih);
+      if (hc == 1) part[j][p] = Ih;
+    }
+    __syncthreads();
+    if (hc == 0) {
+#pragma unroll
+      for (int j = 0; j < kT; ++j) {
+        if (j >= tc) break;
+        const int f = P.f0 + s0 + j;
+        uint32_t nev = 0;
+        int Sp = 0;
+        if (live) {
+          float I = bp[0];
+#pragma unroll
+          for (int c = 0; c < kHalf; ++c) I = fmaf(wp[c], h[j][c], I);
+          I += part[j][p];
+          const float vp = P.beta * V + I;
+          Sp = vp >= P.vth ? 1 : (vp <= -P.vth ? -1 : 0);
+          V = vp - P.reset * (float)Sp;
+          nev = (Sp != 0 && P.t0 + f >= 0) ? 1u : 0u;   // delayed labels below 0: none
+          const int64_t o = (int64_t)(s0 + j) * npix + q;
+          if (I_out) I_out[o] = I;
+          if (spikes) spikes[o] = (int8_t)Sp;
+        }
+        emit_events_warp(events, cap, n_events, nev, (uint32_t)px, (uint32_t)py, (uint32_t)(P.t0 + f), Sp);
       }
-      emit_events_warp(events, cap, n_events, nev, (uint32_t)px, (uint32_t)py, (uint32_t)(P.t0 + f), Sp);
     }
   }
   __syncthreads();
@@ -320,16 +340,17 @@ evsnet_tct_kernel(TctParams P, const float* __restrict__ logl, const float* __re
     // a bounded wait gave up: give the MMAs still in flight a second bounded wait
     mbar_wait(&mma_bar, phase ^ 1u, P.wait_iters);
   } else if (live) {
-    Vg[q] = V;
+    if (hc == 0) Vg[q] = V;
     // the last kt - 1 inputs of every layer back to the state, oldest first
     for (int l = 1; l < L; ++l)
       for (int j = 0; j < hk; ++j) {
-        float v[CP];
-        load_row(slot_of(l, ring_pos(S - hk + j, R)), tid, v);
-        for (int c = 0; c < C; ++c) hist[hidx(l, j, c)] = v[c];
+        float v[kHalf];
+        load_half(slot_of(l, ring_pos(S - hk + j, R)), hc, p, v);
+        for (int c = 0; c < kHalf; ++c)
+          if (c0 + c < C) hist[hidx(l, j, c0 + c)] = v[c];
       }
-    if (ks0 == 0)
-      for (int j = 0; j < hk; ++j) hist[hidx(0, j, 0)] = xh[ring_pos(S - hk + j, R) * TP + tid];
+    if (ks0 == 0 && hc == 0)
+      for (int j = 0; j < hk; ++j) hist[hidx(0, j, 0)] = xh[ring_pos(S - hk + j, R) * TP + p];
   }
   tc_fence_before();
   __syncthreads();
@@ -370,7 +391,7 @@ int et_evsnet_forward_tct(const float* logl, int32_t F, const et_evsnet_weights*
   ET_CHECK_CUDA(cudaGetDevice(&dev));
   ET_CHECK_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   // static shared memory (barrier, TMEM slot, flag) comes on top of the dynamic part
-  if (smem + 1024 > (size_t)max_smem) return ET_ERR_UNIMPLEMENTED;
+  if (smem + 2048 > (size_t)max_smem) return ET_ERR_UNIMPLEMENTED;
   if (P.kt > 1 && !st->hist) return ET_ERR_ARG;
   ET_CHECK_CUDA(cudaFuncSetAttribute(evsnet_tct_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int64_t npix = (int64_t)P.H * P.W;

@@ -220,7 +220,8 @@ extern "C" int et_build_scene_with(const float* tris, const uint32_t* tri_mat, i
                                    const et_quad_light* lights, int32_t n_lights, float env,
                                    int32_t builder_req, et_scene** out, void* stream_) {
   if (!out || n_tris < 0 || n_mats < 0 || n_lights < 0) return ET_ERR_ARG;
-  if (builder_req != ET_BVH_GPU && builder_req != ET_BVH_HOST && builder_req != ET_BVH_SWEEP)
+  if (builder_req != ET_BVH_GPU && builder_req != ET_BVH_HOST && builder_req != ET_BVH_SWEEP &&
+      builder_req != ET_BVH_GPU_SWEEP)
     return ET_ERR_ARG;
   if (n_tris > 0 && (!tris || !tri_mat)) return ET_ERR_ARG;
   if (n_mats > 0 && !mats) return ET_ERR_ARG;
@@ -306,6 +307,8 @@ extern "C" int et_build_scene_with(const float* tris, const uint32_t* tri_mat, i
       grc = ET_OK;
     } else if (builder == ET_BVH_GPU) {
       grc = gpu_binned_sah(v.data(), n, stream, bn_store, perm, depth);
+    } else if (builder == ET_BVH_GPU_SWEEP) {
+      grc = gpu_sweep_sah(v.data(), n, stream, bn_store, perm, depth);
     }
     if (grc != ET_OK || depth > kMaxBvhDepth) {
       if (grc == ET_ERR_CUDA || grc == ET_ERR_OOM) cudaGetLastError();

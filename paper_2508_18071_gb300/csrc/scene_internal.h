@@ -29,7 +29,7 @@ struct et_scene {
   int64_t n_tris = 0, n_nodes = 0;
   double sah = 0.0;
   et_scene_dev dev{};
-  int render_mode = ET_RENDER_WAVEFRONT;
+  int render_mode = ET_RENDER_WAVEFRONT_TILES;
   int builder = ET_BVH_GPU;
   void* wf_mem = nullptr;        // wavefront queues and path state, grown on demand
   int64_t wf_cap = 0, wf_acc_cap = 0;

@@ -42,7 +42,17 @@ struct Batch {
   int s0, ns;          // samples of each frame in this batch
   int64_t npix;        // W * H
   int64_t paths;       // nf * ns * npix
+  int W;               // image width (the slot -> pixel map)
+  int tiled;           // slots visit 8 x 4 pixel tiles (needs W % 8 == 0 and rows % 4 == 0)
 };
+
+// pixel of slot i of a frame's sample plane: raster order, or 8 x 4 tiles in
+// raster order of tiles (a warp's 32 primary rays then cover a compact tile)
+__host__ __device__ __forceinline__ int64_t slot_pixel(const Batch& bt, int64_t i) {
+  if (!bt.tiled) return i;
+  const int64_t tile = i >> 5, tx = tile % (bt.W >> 3), ty = tile / (bt.W >> 3);
+  return (ty * 4 + ((i >> 3) & 3)) * bt.W + tx * 8 + (i & 7);
+}
 
 struct Args {
   et_scene_dev S;
@@ -65,7 +75,7 @@ struct Args {
 
 // path q of the batch -> (frame of the call, sample, pixel)
 __device__ __forceinline__ void path_ids(const Batch& bt, int64_t q, int& f, int& s, int64_t& pix) {
-  pix = q % bt.npix;
+  pix = slot_pixel(bt, q % bt.npix);
   const int64_t plane = q / bt.npix;
   s = bt.s0 + (int)(plane % bt.ns);
   f = bt.f0 + (int)(plane / bt.ns);
@@ -253,16 +263,16 @@ wf_accumulate(Args A, float4* acc, bool first_slice, bool last_slice, float* rgb
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (int64_t)A.bt.nf * A.bt.npix) return;
   const int fb = (int)(i / A.bt.npix);
-  const int64_t pix = i % A.bt.npix;
+  const int64_t slot = i % A.bt.npix;
   f3 a = mk(0.0f, 0.0f, 0.0f);
   if (!first_slice) { const float4 t = acc[i]; a = mk(t.x, t.y, t.z); }
   for (int sb = 0; sb < A.bt.ns; ++sb) {
-    const float4 l = A.L[((int64_t)fb * A.bt.ns + sb) * A.bt.npix + pix];
+    const float4 l = A.L[((int64_t)fb * A.bt.ns + sb) * A.bt.npix + slot];
     a = a + mk(l.x, l.y, l.z);
   }
   if (!last_slice) { acc[i] = make_float4(a.x, a.y, a.z, 0.0f); return; }
   const f3 m = a * (1.0f / (float)A.spp);
-  const int64_t o = (int64_t)(A.bt.f0 + fb) * A.bt.npix + pix;
+  const int64_t o = (int64_t)(A.bt.f0 + fb) * A.bt.npix + slot_pixel(A.bt, slot);
   if (rgb) { rgb[3 * o] = m.x; rgb[3 * o + 1] = m.y; rgb[3 * o + 2] = m.z; }
   if (logl) logl[o] = pt::log_luminance(m, log_mode, log_param);
 }
@@ -289,6 +299,8 @@ int et_render_wavefront(et_scene* s, int n_frames, int first_frame, int W, int H
   const int64_t planes = std::max<int64_t>(1, kPathCap / npix);
   Batch proto{};
   proto.npix = npix;
+  proto.W = W;
+  proto.tiled = s->render_mode == ET_RENDER_WAVEFRONT_TILES && W % 8 == 0 && (y1 - y0) % 4 == 0;
   int frames_per_batch, samples_per_batch;
   if (spp <= planes) {
     samples_per_batch = spp;

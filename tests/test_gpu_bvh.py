@@ -1,9 +1,11 @@
 """The hierarchy builders.  The GPU binned-SAH build's SAH cost stays within
-10 % of the oracle's full-sweep SAH (P14); the host full-sweep build (the
-default) runs the oracle's algorithm and lands within 2 % of its cost (FP32
-bounds against FP64).  Closest hits through either hierarchy equal the
-oracle's brute-force answers (records of the first path segment), including
-degenerate inputs (coincident centroids, a single triangle)."""
+10 % of the oracle's full-sweep SAH (P14); the full-sweep builds -- on the
+device (the default) and on the host -- run the oracle's algorithm and land
+within 2 % of its cost (FP32 bounds against FP64), and the device sweep builds
+the host sweep's tree: the same node count and SAH cost, and the same
+radiance.  Closest hits through every hierarchy equal the oracle's brute-force
+answers (records of the first path segment), including degenerate inputs
+(coincident centroids, a single triangle)."""
 import time
 
 import numpy as np
@@ -22,7 +24,7 @@ def api():
     return A
 
 
-@pytest.mark.parametrize("builder", ["gpu", "sweep"])
+@pytest.mark.parametrize("builder", ["gpu", "sweep", "gpu_sweep"])
 @pytest.mark.parametrize("name", ["cornell", "random", "city"])
 def test_builder_quality(api, orc, name, builder):
     s = {"cornell": inputs.cornell_box, "random": lambda: inputs.random_scene(seed=11),
@@ -42,8 +44,26 @@ def test_builder_quality(api, orc, name, builder):
           % (name, builder, info["n_tris"], dt, info["sah_cost"], o.sah_cost()))
 
 
-def test_default_builder_is_sweep(api):
-    assert api.Scene(inputs.cornell_box()).info()["builder"] == "sweep"
+def test_default_builder_is_the_gpu_sweep(api):
+    assert api.Scene(inputs.cornell_box()).info()["builder"] == "gpu_sweep"
+
+
+@pytest.mark.parametrize("name", ["random", "city"])
+def test_gpu_sweep_builds_the_host_sweep_tree(api, name):
+    """Same algorithm, same split order and node numbering: the device sweep's
+    hierarchy has the host sweep's node count and SAH cost (the splits' costs
+    are compared in double on both sides; a tie broken differently by a fused
+    multiply-add in one of the two compilers would move a split, so the cost is
+    compared to 1e-9) and renders the same image."""
+    s = {"random": lambda: inputs.random_scene(seed=11), "city": lambda: inputs.city_block(seed=21)}[name]()
+    a, b = api.Scene(s, builder="gpu_sweep"), api.Scene(s, builder="sweep")
+    ia, ib = a.info(), b.info()
+    assert ia["n_nodes"] == ib["n_nodes"]
+    assert abs(ia["sah_cost"] / ib["sah_cost"] - 1.0) <= 1e-9, (ia, ib)
+    cams = inputs.city_path(2, first=300) if name == "city" else inputs.random_scene_path(2, first=10)
+    ra = api.render_frames(a, cams, 160, 90, 2, 5, 3, want_logl=False)[0].cpu().numpy()
+    rb = api.render_frames(b, cams, 160, 90, 2, 5, 3, want_logl=False)[0].cpu().numpy()
+    assert np.array_equal(ra, rb)
 
 
 def _first_hits_match_brute_force(api, orc, s, cams, W, H, builder):
@@ -58,7 +78,7 @@ def _first_hits_match_brute_force(api, orc, s, cams, W, H, builder):
     return g
 
 
-@pytest.mark.parametrize("builder", ["gpu", "sweep"])
+@pytest.mark.parametrize("builder", ["gpu", "sweep", "gpu_sweep"])
 def test_degenerate_coincident_centroids(api, orc, builder):
     # 40 copies of one triangle plus a few others: every split of the copies is
     # by position; the closest hit must pick the lowest index among equal t
@@ -73,7 +93,7 @@ def test_degenerate_coincident_centroids(api, orc, builder):
     assert g.info()["builder"] == builder
 
 
-@pytest.mark.parametrize("builder", ["gpu", "sweep"])
+@pytest.mark.parametrize("builder", ["gpu", "sweep", "gpu_sweep"])
 def test_single_triangle_and_random_soup(api, orc, builder):
     s = {"tris": np.array([[-1, -1, -2, 1, -1, -2, 0, 1, -2]], np.float32),
          "tri_mat": np.zeros(1, np.uint32), "materials": np.asarray([[0.5, 0.5, 0.5, 0.5, 0]], np.float32),
