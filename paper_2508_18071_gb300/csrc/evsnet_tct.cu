@@ -24,6 +24,14 @@
 // by this kernel are BF16-rounded, so a later call of the BF16 path reads them
 // back exactly.
 //
+// The 3 x 3 stem's input: when the image width is a multiple of 128 (a tile is
+// then one row segment), each chunk's log frames f - 1 .. f + 1, rows y - 1 ..
+// y + 1 and columns x0 - 4 .. x0 + 131 arrive as one TMA box
+// (cp.async.bulk.tensor.3d; the tensor map covers the caller's log frames,
+// zero-filled outside the image, which is the stem's zero padding), issued one
+// chunk ahead by one thread and waited on through an mbarrier; the first chunk
+// of a call, whose previous frame may be the state's, is loaded by the threads.
+//
 // MMA waits are bounded; on expiry the kernel sets bit 62 of the event count,
 // leaves the membrane and history state untouched, waits (bounded) for its
 // MMAs in flight and frees its TMEM.
@@ -31,7 +39,9 @@
 #include "event_emit.cuh"
 #include "evsnet_common.h"
 #include "tc_ptx.cuh"
+#include <cuda.h>
 #include <cuda_bf16.h>
+#include <cstring>
 
 namespace {
 
@@ -46,6 +56,7 @@ constexpr int kHalf = CP / 2;            // channels per thread
 constexpr int kThreads = 2 * TP;
 constexpr uint32_t kTmemCols = 32;      // kT x 16 accumulator columns
 constexpr unsigned long long kTimeoutBit = 1ull << 62;
+constexpr uint32_t kDrainIters = 1u << 22;   // bound of the waits for work in flight after a bail
 
 struct TctParams {
   int H, W, F, f0, t0;
@@ -53,9 +64,15 @@ struct TctParams {
   float beta, vth, reset;
   int R;                                // ring slots per layer: kt + kT - 1
   int woff[kMaxLayers + 1];             // packed weight offsets per layer (+ projection)
-  int off_wB, off_f32;                  // shared-memory byte offsets
+  int off_wB, off_f32, off_xbuf;        // shared-memory byte offsets
+  int tma;                              // the stem's input tiles come by TMA
   uint32_t wait_iters;
 };
+
+// the TMA box of the 3 x 3 stem: columns x0 - 4 .. x0 + 131, 3 rows, 3 frames
+constexpr int kBoxW = TP + 8;
+constexpr int kBoxFloats = kBoxW * 3 * 3;
+constexpr uint32_t kBoxBytes = kBoxFloats * 4;
 
 __device__ __forceinline__ int ring_pos(int s, int R) { return ((s % R) + R) % R; }
 
@@ -90,13 +107,14 @@ __device__ __forceinline__ void load_half(const unsigned char* slot, int hc, int
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
-evsnet_tct_kernel(TctParams P, const float* __restrict__ logl, const float* __restrict__ wg,
-                  const float* __restrict__ bg, float* __restrict__ Vg, float* __restrict__ hist,
-                  const float* __restrict__ last_l, et_event* events, int64_t cap,
+evsnet_tct_kernel(const __grid_constant__ CUtensorMap tmap, TctParams P, const float* __restrict__ logl,
+                  const float* __restrict__ wg, const float* __restrict__ bg, float* __restrict__ Vg,
+                  float* __restrict__ hist, const float* __restrict__ last_l, et_event* events, int64_t cap,
                   unsigned long long* n_events, float* __restrict__ I_out,
                   int8_t* __restrict__ spikes) {
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ uint64_t mma_bar;
+  __shared__ uint64_t tma_bar;
   __shared__ uint32_t tmem_slot;
   __shared__ int bail;
   __shared__ float part[kT][TP];        // the second half's share of the projection
@@ -118,6 +136,7 @@ evsnet_tct_kernel(TctParams P, const float* __restrict__ logl, const float* __re
   float* w0 = bp + 4;                                          // [taps][CP] layer 0
   const int taps0 = ks0 > 0 ? ks0 * ks0 : kt;
   float* xh = w0 + taps0 * CP;                                 // [R][TP] layer-0 X ring (temporal layer 0)
+  float* xbuf = reinterpret_cast<float*>(sm + P.off_xbuf);     // [3 frames][3 rows][kBoxW] (TMA)
   auto slot_of = [&](int l, int pos) { return rings + ((size_t)(l - 1) * R + pos) * kSlot; };
   // history element (layer l, oldest-first slot j, channel c) of this pixel in the state
   auto hidx = [&](int l, int j, int c) -> int64_t { return (((int64_t)l * hk + j) * C + c) * npix + q; };
@@ -158,7 +177,7 @@ evsnet_tct_kernel(TctParams P, const float* __restrict__ logl, const float* __re
   }
   float V = (live && hc == 0) ? Vg[q] : 0.0f;
   if (warp == 0) tmem_alloc(&tmem_slot, kTmemCols);
-  if (tid == 0) { mbar_init(&mma_bar, 1); bail = 0; }
+  if (tid == 0) { mbar_init(&mma_bar, 1); mbar_init(&tma_bar, 1); bail = 0; }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -189,9 +208,32 @@ evsnet_tct_kernel(TctParams P, const float* __restrict__ logl, const float* __re
     }
   };
   if (ks0 == 3) load_x9(0);
+  // TMA of the stem's input: the tile's row segment (tiles are whole row
+  // segments when it is used), one box per chunk
+  const int tx0 = (int)(((int64_t)blockIdx.x * TP) % P.W), ty0 = (int)(((int64_t)blockIdx.x * TP) / P.W);
+  uint32_t tma_phase = 0;
+  bool tma_pending = false;
   for (int s0 = 0; s0 < S && !bail; s0 += kT) {
     const int tc = min(kT, S - s0);
     const int pc = ring_pos(s0, R);     // ring position of the chunk's first step
+    if (P.tma && s0 > 0) {
+      // this chunk's box, issued during the previous chunk
+      if (!mbar_wait(&tma_bar, tma_phase, P.wait_iters)) {
+        if (lane == 0) atomicOr(n_events, kTimeoutBit);
+        bail = 1;
+      }
+      tma_phase ^= 1;
+      tma_pending = false;
+      __syncthreads();
+      if (bail) break;
+#pragma unroll
+      for (int j = 0; j < kT; ++j)
+#pragma unroll
+        for (int t = 0; t < 9; ++t) {
+          const int col = p + t % 3 + 3, row = t / 3;
+          xn[j][t] = xbuf[((1 + j) * 3 + row) * kBoxW + col] - xbuf[(j * 3 + row) * kBoxW + col];
+        }
+    }
     float h[kT][kHalf];                 // block input (residual) / current activation, FP32
     // ---- layer 0 on CUDA cores, FP32: X_k = l_k - l_{k-1} (Eq. 1)
 #pragma unroll
@@ -243,13 +285,20 @@ evsnet_tct_kernel(TctParams P, const float* __restrict__ logl, const float* __re
       const int pj = pc + j >= R ? pc + j - R : pc + j;
       store_half(slot_of(1, pj), hc, p, h[j]);
     }
-    if (ks0 == 3) load_x9(s0 + kT);   // next chunk's inputs, consumed after these layers
+    if (ks0 == 3 && !P.tma) load_x9(s0 + kT);   // next chunk's inputs, consumed after these layers
     // ---- layers 1 .. L-1 on the tensor core
     for (int l = 1; l < L; ++l) {
       fence_proxy_async_smem();
       tc_fence_before();
       __syncthreads();
       tc_fence_after();
+      if (l == 1 && P.tma && tid == 0 && s0 + kT < S) {
+        // the next chunk's stem input (this chunk's was read before the barrier
+        // above, and every thread's proxy fence orders those reads first)
+        mbar_arrive_expect_tx(&tma_bar, kBoxBytes);
+        tma_load_3d(xbuf, &tmap, tx0 - 4, ty0 - 1, P.f0 + s0 + kT - 1, &tma_bar);
+      }
+      if (l == 1 && P.tma && s0 + kT < S) tma_pending = true;
       if (tid == 0) {
         // descriptors differ only in their start-address field (16-byte units):
         // slots are 4 KB apart, B blocks 512 B
@@ -337,8 +386,10 @@ evsnet_tct_kernel(TctParams P, const float* __restrict__ logl, const float* __re
   }
   __syncthreads();
   if (bail) {
-    // a bounded wait gave up: give the MMAs still in flight a second bounded wait
-    mbar_wait(&mma_bar, phase ^ 1u, P.wait_iters);
+    // a bounded wait gave up: give the MMAs and the TMA still in flight a
+    // second bounded wait
+    mbar_wait(&mma_bar, phase ^ 1u, kDrainIters);
+    if (tma_pending) mbar_wait(&tma_bar, tma_phase, kDrainIters);
   } else if (live) {
     if (hc == 0) Vg[q] = V;
     // the last kt - 1 inputs of every layer back to the state, oldest first
@@ -383,10 +434,40 @@ int et_evsnet_forward_tct(const float* logl, int32_t F, const et_evsnet_weights*
   const size_t rings = (size_t)(P.L - 1) * P.R * kSlot;
   const size_t wbytes = (size_t)(P.L - 1) * P.kt * CP * CP * 2;
   const int taps0 = P.ks0 > 0 ? P.ks0 * P.ks0 : P.kt;
-  const size_t fbytes = sizeof(float) * ((size_t)P.L * CP + CP + 4 + (size_t)taps0 * CP + (size_t)P.R * TP);
+  // the X ring of a temporal layer 0 (not kept with a stem)
+  const size_t fbytes = sizeof(float) * ((size_t)P.L * CP + CP + 4 + (size_t)taps0 * CP +
+                                         (P.ks0 == 0 ? (size_t)P.R * TP : 0));
   P.off_wB = (int)rings;
   P.off_f32 = (int)(rings + wbytes);
-  const size_t smem = rings + wbytes + fbytes;
+  // TMA of the 3 x 3 stem's input: tiles must be row segments and the frames'
+  // base and row pitch 16-byte aligned
+  CUtensorMap tmap;
+  std::memset(&tmap, 0, sizeof(tmap));
+  P.tma = P.ks0 == 3 && P.W % TP == 0 && (reinterpret_cast<uintptr_t>(logl) & 15) == 0 && F >= 1;
+  P.off_xbuf = (int)(((size_t)P.off_f32 + fbytes + 127) & ~(size_t)127);
+  const size_t smem = (size_t)P.off_xbuf + (P.tma ? (size_t)kBoxBytes : 0);
+  if (P.tma) {
+    typedef CUresult (*EncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    static EncodeFn encode = nullptr;
+    if (!encode) {
+      void* f = nullptr;
+      cudaDriverEntryPointQueryResult qr;
+      if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &qr) !=
+              cudaSuccess || qr != cudaDriverEntryPointSuccess || !f)
+        return ET_ERR_CUDA;
+      encode = reinterpret_cast<EncodeFn>(f);
+    }
+    const cuuint64_t dims[3] = {(cuuint64_t)P.W, (cuuint64_t)P.H, (cuuint64_t)F};
+    const cuuint64_t strides[2] = {(cuuint64_t)P.W * 4, (cuuint64_t)P.W * P.H * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)kBoxW, 3, 3};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    if (encode(&tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(logl), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return ET_ERR_CUDA;
+  }
   int dev = 0, max_smem = 0;
   ET_CHECK_CUDA(cudaGetDevice(&dev));
   ET_CHECK_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
@@ -396,7 +477,7 @@ int et_evsnet_forward_tct(const float* logl, int32_t F, const et_evsnet_weights*
   ET_CHECK_CUDA(cudaFuncSetAttribute(evsnet_tct_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int64_t npix = (int64_t)P.H * P.W;
   evsnet_tct_kernel<<<(unsigned)((npix + TP - 1) / TP), kThreads, smem, stream>>>(
-      P, logl, net->w, net->b, st->V, st->hist, st->last_l, events, cap,
+      tmap, P, logl, net->w, net->b, st->V, st->hist, st->last_l, events, cap,
       reinterpret_cast<unsigned long long*>(n_events), I_out, spikes);
   ET_CHECK_LAUNCH();
   return ET_OK;

@@ -17,6 +17,9 @@ Bars:
     against the FP32 path;
   * chunked calls equal one call bit for bit; a forced wait timeout leaves the
     state untouched and the next call exact.
+Widths that are multiples of 128 take the stem's input through TMA boxes (the
+first chunk of a call through the threads), the others through thread loads:
+both are covered.
 """
 import numpy as np
 import pytest
@@ -103,9 +106,10 @@ def _run(api, d, lf, dtype, chunks=None):
 
 @pytest.mark.parametrize("form,H,W,dens", [((1, 7, 16, 7, 0), 9, 11, 0.05),     # paper form, k 7, M 3
                                             ((1, 7, 16, 7, 3), 23, 37, 0.05),    # 3 x 3 stem + blocks
+                                            ((1, 7, 16, 7, 3), 7, 256, 0.05),    # stem input by TMA
                                             ((0, 3, 8, 5, 0), 16, 16, 0.1),      # plain stack, C 8
                                             ((1, 5, 16, 7, 5), 13, 29, 0.03)],   # 5 x 5 stem, M 2
-                         ids=["paper", "stem3", "stack_C8", "stem5_M2"])
+                         ids=["paper", "stem3", "stem3_tma", "stack_C8", "stem5_M2"])
 def test_tct_bf16_exact_on_dyadic_data(api, orc, form, H, W, dens):
     from paper_2508_18071_gb300 import _lib
     d = _dyadic_net(*form, seed=4, dens=dens)
@@ -124,7 +128,7 @@ def test_tct_bf16_exact_on_dyadic_data(api, orc, form, H, W, dens):
     assert np.array_equal(_sorted(ev16), _sorted(ev32))
 
 
-@pytest.mark.parametrize("ks0,H,W", [(0, 21, 19), (3, 40, 51)])
+@pytest.mark.parametrize("ks0,H,W", [(0, 21, 19), (3, 40, 51), (3, 11, 384)])
 def test_tct_bf16_random_weights_vs_oracle_bf16_mode(api, orc, ks0, H, W):
     from paper_2508_18071_gb300 import _lib
     d = inputs.random_evsnet(1, 7, 16, 7, 1, seed=12, std=0.15, vth=0.1, beta=0.95, ks0=ks0)
@@ -173,7 +177,8 @@ def test_tct_bf16_full_size_sampled(api, orc):
         assert close.mean() >= 0.99, (y0, x0, close.mean())
 
 
-def test_tct_forced_timeout_leaves_state(api):
+@pytest.mark.parametrize("W", [23, 128])
+def test_tct_forced_timeout_leaves_state(api, W):
     """et_set_wait_budget(0): the first MMA wait gives up, the call reports
     ET_ERR_TIMEOUT through the count's flag bit and leaves the membrane and the
     history untouched; with the budget restored a fresh state gives the same
@@ -181,13 +186,13 @@ def test_tct_forced_timeout_leaves_state(api):
     from paper_2508_18071_gb300 import _lib
     lib = _lib.load()
     d = inputs.random_evsnet(1, 7, 16, 7, 1, seed=3, std=0.15, vth=0.1, beta=0.95, ks0=3)
-    lf = torch.as_tensor(inputs.random_logl_clip(2, 12, 17, 23, step_std=0.3)).cuda()
+    lf = torch.as_tensor(inputs.random_logl_clip(2, 12, 17, W, step_std=0.3)).cuda()
     net = api.EvsNetDev.from_dict(d, _lib.ET_BF16)
-    ref = api.evsnet_forward(lf, net, api.EvsStateDev(net, 17, 23))[0].host()
+    ref = api.evsnet_forward(lf, net, api.EvsStateDev(net, 17, W))[0].host()
     assert len(ref) > 0
     try:
         lib.et_set_wait_budget(0)
-        st = api.EvsStateDev(net, 17, 23)
+        st = api.EvsStateDev(net, 17, W)
         st.hist.normal_()
         V0, h0 = st.V.clone(), st.hist.clone()
         buf = api.evsnet_forward(lf, net, st)[0]
@@ -198,5 +203,5 @@ def test_tct_forced_timeout_leaves_state(api):
     finally:
         lib.et_set_wait_budget(-1)
     torch.cuda.synchronize()
-    again = api.evsnet_forward(lf, net, api.EvsStateDev(net, 17, 23))[0].host()
+    again = api.evsnet_forward(lf, net, api.EvsStateDev(net, 17, W))[0].host()
     assert np.array_equal(_sorted(again), _sorted(ref))
