@@ -57,6 +57,11 @@ def parse():
                    help="hierarchy builder (default: the library's)")
     p.add_argument("--no-sweep", action="store_true",
                    help="skip the EvSNet precision sweep (FP32 / BF16 / FP8) after the timed region")
+    p.add_argument("--net", default="stem", choices=sorted(NETS),
+                   help="trained city network: 3x3 stem + temporal blocks (the default), the "
+                        "paper's temporal form, or the 3x3 stack (profiling cases)")
+    p.add_argument("--sweep-frames", type=int, default=2000,
+                   help="precision sweep: EvSNet steps at 1280x720, 1 spp")
     p.add_argument("--rows", action="store_true",
                    help="measure the rows beside the benchmark's path (event generators, "
                         "annotations, refit, training, FP32 EvSNet) instead of the metric")
@@ -65,10 +70,13 @@ def parse():
     return p.parse_args()
 
 
-def load_net(dtype):
+NETS = {"stem": "evsnet_city.npz", "temporal": "evsnet_city_temporal.npz", "3x3": "evsnet_city_spatial.npz"}
+
+
+def load_net(dtype, form="stem"):
     """Trained EvSNet weights if present, else random-init weights of the same shape."""
     from paper_2508_18071_gb300 import api
-    _, d = load_net_host()
+    _, d = load_net_host(form)
     return api.EvsNetDev.from_dict(d, dtype), d
 
 
@@ -193,7 +201,7 @@ def run_reference(args):
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     scene = inputs.city_block(seed=21)
     o = oracle.Scene(scene["tris"], scene["tri_mat"], scene["materials"], scene["lights"], scene["env"])
-    _, net_d = load_net_host()
+    _, net_d = load_net_host(args.net)
     onet = oracle.EvsNet.from_dict(net_d)
     rows_per_step = 4
     times, walls = [], []
@@ -232,41 +240,75 @@ def run_reference(args):
     print(json.dumps(line))
 
 
-def precision_sweep(api, _lib, net_d, logl, stream, reps=5):
-    """EvSNet alone on the last step's rendered frames in each precision: device
-    time per frame, tensor throughput, and events against the FP32 path (F1 with
-    no spatial or temporal tolerance)."""
+def precision_sweep(api, frames, spp, peaks, n_sm, chunk=250):
+    """The precision sweep on its own workload: `frames` + 1 frames of the city
+    block at 1280 x 720 and `spp` SPP, rendered once, then EvSNet alone over all
+    of them in every precision the network's form has a kernel for (the trained
+    stem network; the trained 3 x 3 stack, which also has FP8; a random-init
+    3 x 3 stack): device time per frame, throughput against its peak, events,
+    and F1 and EMD against the FP32 output of the same network."""
     import torch
-    F, H, W = logl.shape
-    flops = 2.0 * macs_per_pixel_step(net_d) * H * W * (F - 1)
-    out, ev_ref = {}, None
-    for name, dt in (("f32", _lib.ET_F32), ("bf16", _lib.ET_BF16), ("fp8", _lib.ET_FP8)):
-        net = api.EvsNetDev.from_dict(net_d, dt)
-        buf = api.EventBuffer(F * H * W)
-        ts = []
-        try:
-            api.evsnet_forward(logl[:2].contiguous(), net, api.EvsStateDev(net, H, W), t0=0, buf=buf)
-        except _lib.ETError as e:
-            out[name] = {"unsupported": str(e)}
-            continue
-        for r in range(reps + 1):
-            st = api.EvsStateDev(net, H, W)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            api.evsnet_forward(logl, net, st, t0=0, buf=buf)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            if r > 0:
-                ts.append(e0.elapsed_time(e1))
-        ev = buf.host()
-        if ev_ref is None:
-            ev_ref = ev
-        ms = statistics.median(ts)
-        out[name] = {"ms_per_frame": ms / (F - 1), "tflops": flops / (ms / 1e3) / 1e12,
-                     "events": len(ev), "f1_vs_f32": api.event_f1(ev, ev_ref, 0)}
-    out["frames"] = F - 1
-    out["note"] = "first frame only sets the state; median of %d calls" % reps
+    from paper_2508_18071_gb300 import inputs
+    from paper_2508_18071_gb300 import precision_sweep as ps
+    F = frames + 1
+    sc = inputs.city_block(seed=21)
+    g = api.Scene(sc)
+    cams = inputs.city_path(F)
+    logl = torch.empty((F, H_, W_), dtype=torch.float32, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for f0 in range(0, F, chunk):
+        f1 = min(F, f0 + chunk)
+        api.render_frames(g, cams[f0:f1], W_, H_, spp, DEPTH, SEED, first_frame=f0, logl=logl[f0:f1],
+                          want_rgb=False)
+    e1.record()
+    torch.cuda.synchronize()
+    out = {"workload": "city block %d tris, %dx%d, %d steps (%d frames) at 1 kHz, %d spp, depth %d"
+                       % (len(sc["tris"]) + 2 * len(sc["lights"]), W_, H_, frames, F, spp, DEPTH),
+           "render_ms_per_frame": e0.elapsed_time(e1) / F}
+    del g
+    bf = peaks.get("bf16_tflops_sustained") or 1700.0
+    pk = {"f32": (n_sm * FP32_LANES_PER_SM * 2 * 2.07e9 / 1e12, "derived FP32 peak (not measured)"),
+          "bf16": (bf, "measured sustained bf16 (of measured)" if "bf16_tflops_sustained" in peaks
+                   else "fallback 1.7 PFLOP/s"),
+          "fp8": (2.0 * bf, "measured sustained bf16 x 2 (nominal fp8 / bf16 ratio)")}
+    for key, res in ps.run_nets(logl).items():
+        for dt, r in res.items():
+            if "tflops" in r:
+                r["frac_of_peak"] = r["tflops"] / pk[dt][0]
+                r["peak_source"] = pk[dt][1]
+        out[key] = res
+    out["note"] = ("dense spike output timed with each call (1 B per pixel-step); F1 matches spikes "
+                   "per pixel and step (delta 0); EMD is the paper's bidirectional loss (Eq. 8-9) "
+                   "between the two spike trains, mean over pixels; tensor-pipe counters in profiles/")
+    del logl
+    torch.cuda.empty_cache()
     return out
+
+
+def render_mrays(api, g, cams, W, H, spp, first, reps=3):
+    """Mrays/s of the wavefront renderer on one camera segment: rays traced
+    (closest-hit and shadow queries, counted by the render profiler) over the
+    device time of a plain render (median of `reps`)."""
+    import torch
+    ts = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        api.render_frames(g, cams, W, H, spp, DEPTH, SEED, first_frame=first, want_rgb=False)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    g.profile(True)
+    api.render_frames(g, cams, W, H, spp, DEPTH, SEED, first_frame=first, want_rgb=False)
+    prof = g.profile_read()
+    g.profile(False)
+    rays = prof["trace"][2] + prof["shadow"][2]
+    ms = statistics.median(ts)
+    return {"mrays_per_s": rays / (ms / 1e3) / 1e6, "rays": rays, "frames": len(cams),
+            "ms_per_frame": ms / len(cams),
+            "note": "closest-hit plus shadow rays counted by the render profiler; device time of "
+                    "the plain render, median of %d" % reps}
 
 
 def run_rows(args):
@@ -551,12 +593,13 @@ def event_gate_c2(api, inputs, dev, stream, nb=101, warm=64, spp=4, W=256, H=256
                                        ref_ev),
             "ceiling_second_256spp_render": _f1s(api, _win(_thr(api, hi2, s0, dev), lo, hi), ref_ev),
             "ceiling_1024spp_render": _f1s(api, _win(_thr(api, hq, s0, dev), lo, hi), ref_ev),
-            "n_ref": len(ref_ev), "n_method": len(m_ev)}
+            "n_ref": len(ref_ev), "n_method": len(m_ev),
+            "render": render_mrays(api, g, cams[warm:warm + 100], W, H, spp, s0)}
 
 
-def load_net_host():
+def load_net_host(form="stem"):
     from paper_2508_18071_gb300 import inputs, train_evsnet
-    path = os.path.join(ROOT, "paper_2508_18071_gb300", "weights", "evsnet_city.npz")
+    path = os.path.join(ROOT, "paper_2508_18071_gb300", "weights", NETS[form])
     if os.path.exists(path):
         return None, train_evsnet.load(path)
     d = inputs.random_evsnet(0, 4, 16, 1, 3, seed=12, vth=0.5, beta=0.9)
@@ -595,7 +638,7 @@ def main():
     info["build_s"] = time.perf_counter() - tb0
     if args.evsnet_dtype == "auto":
         # BF16 where the library has a tensor-core kernel for the network's form
-        _, d_probe = load_net_host()
+        _, d_probe = load_net_host(args.net)
         probe = api.EvsNetDev.from_dict(d_probe, _lib.ET_BF16)
         try:
             api.evsnet_forward(torch.zeros((2, 8, 8), device=dev), probe, api.EvsStateDev(probe, 8, 8))
@@ -603,7 +646,7 @@ def main():
         except _lib.ETError:
             args.evsnet_dtype = "f32"
     dtype = {"f32": _lib.ET_F32, "bf16": _lib.ET_BF16, "fp8": _lib.ET_FP8}[args.evsnet_dtype]
-    net, net_d = load_net(dtype)
+    net, net_d = load_net(dtype, args.net)
     F = args.frames
     # the partition across ranks: row bands (each rank renders its rows of every
     # frame plus the halo its EvSNet reads, and keeps its own rows' events; the
@@ -758,8 +801,6 @@ def main():
                                "unit": "TFLOP/s", "frac": flops_evs / t_evs_s / 1e12 / pk,
                                "traffic": None, "peak_source": src,
                                "work": "%d MAC per pixel-step (%s)" % (macs, net_desc(net_d))}
-    if not args.no_sweep:
-        line["evsnet_precision_sweep"] = precision_sweep(api, _lib, net_d, logl, stream)
     if rank != 0:
         return
 
@@ -851,6 +892,9 @@ def main():
         line["event_f1_vs_baseline"] = gate
         if not args.no_c2:
             line["event_f1_c2"] = event_gate_c2(api, inputs, dev, stream)
+    if not args.no_sweep:
+        line["evsnet_precision_sweep"] = precision_sweep(api, args.sweep_frames, 1, peaks,
+                                                         props.multi_processor_count)
     print(json.dumps(line))
 
 

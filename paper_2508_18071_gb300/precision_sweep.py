@@ -7,8 +7,9 @@ the FP32 output (the paper's Eq. 8-9, averaged over pixels).
 
     python -m paper_2508_18071_gb300.precision_sweep [--frames 2000] [--spp 1]
 
-Prints one JSON object.  Networks: the trained city network and a random-init
-one of the same shape (N(0, 0.1) weights, Vth 0.5, leak 0.9).
+Prints one JSON object.  Networks: the trained city networks (the stem form
+and the 3x3 stack) and a random-init 3x3 stack (N(0, 0.1) weights, Vth 0.5,
+leak 0.9); precisions a form has no kernel for are listed as unsupported.
 """
 from __future__ import annotations
 
@@ -37,15 +38,29 @@ def _time(fn, reps=3):
     return min(ts)
 
 
+def macs_per_pixel_step(d: dict) -> int:
+    """Multiply-adds of one pixel-step: every conv layer (a stem layer 0 is one
+    step by ks0 x ks0) plus the projection."""
+    C, Ln, kt, ks, ks0 = d["C"], d["n_layers"], d["kt"], d["ks"], int(d.get("ks0", 0))
+    first = C * ks0 * ks0 if ks0 > 0 else C * kt * ks * ks
+    return first + (Ln - 1) * C * C * kt * ks * ks + C
+
+
 def sweep(logl: torch.Tensor, net_d: dict, cap=1 << 20) -> dict:
+    """Each precision the network's form has a kernel for (others are listed
+    as unsupported)."""
     F, H, W = logl.shape
     K = F - 1
-    C, Ln = net_d["C"], net_d["n_layers"]
-    flops = 2.0 * (9 * C + (Ln - 1) * 9 * C * C + C) * H * W * K
+    flops = 2.0 * macs_per_pixel_step(net_d) * H * W * K
     out, ref = {}, None
     buf = api.EventBuffer(cap)
     for name, dt in (("f32", L.ET_F32), ("bf16", L.ET_BF16), ("fp8", L.ET_FP8)):
         net = api.EvsNetDev.from_dict(net_d, dt)
+        try:
+            api.evsnet_forward(logl[:2].contiguous(), net, api.EvsStateDev(net, H, W), buf=buf)
+        except L.ETError as e:
+            out[name] = {"unsupported": str(e)}
+            continue
         holder = {}
 
         def call():
@@ -75,7 +90,6 @@ def main():
     p.add_argument("--height", type=int, default=720)
     p.add_argument("--chunk", type=int, default=200)
     a = p.parse_args()
-    from . import train_evsnet
     scene = api.Scene(inputs.city_block(seed=21))
     path = inputs.city_path(a.frames)
     logl = torch.empty((a.frames, a.height, a.width), dtype=torch.float32, device="cuda")
@@ -88,11 +102,22 @@ def main():
     res = {"workload": "city block 500k triangles, %dx%d, %d frames at 1 kHz, %d SPP, depth 5"
                        % (a.width, a.height, a.frames, a.spp),
            "render_s": time.time() - t0}
-    trained = train_evsnet.load(os.path.join(HERE, "weights", "evsnet_city.npz"))
-    rand = inputs.random_evsnet(0, 4, 16, 1, 3, seed=12, vth=0.5, beta=0.9)
-    res["trained"] = sweep(logl, trained)
-    res["random_init"] = sweep(logl, rand)
+    res.update(run_nets(logl))
     print(json.dumps(res))
+
+
+def run_nets(logl: torch.Tensor) -> dict:
+    """The sweep for the trained city networks (the stem form the benchmark
+    runs, and the four-layer 3x3 stack, whose form also has an FP8 kernel) and
+    a random-init 3x3 stack (N(0, 0.1) weights, Vth 0.5, leak 0.9)."""
+    from . import train_evsnet
+    res = {}
+    for key, fn in (("trained_stem", "evsnet_city.npz"), ("trained_3x3", "evsnet_city_spatial.npz")):
+        path = os.path.join(HERE, "weights", fn)
+        if os.path.exists(path):
+            res[key] = sweep(logl, train_evsnet.load(path))
+    res["random_init_3x3"] = sweep(logl, inputs.random_evsnet(0, 4, 16, 1, 3, seed=12, vth=0.5, beta=0.9))
+    return res
 
 
 if __name__ == "__main__":
