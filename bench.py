@@ -278,9 +278,10 @@ def precision_sweep(api, frames, spp, peaks, n_sm, chunk=250):
                 r["frac_of_peak"] = r["tflops"] / pk[dt][0]
                 r["peak_source"] = pk[dt][1]
         out[key] = res
-    out["note"] = ("dense spike output timed with each call (1 B per pixel-step); F1 matches spikes "
-                   "per pixel and step (delta 0); EMD is the paper's bidirectional loss (Eq. 8-9) "
-                   "between the two spike trains, mean over pixels; tensor-pipe counters in profiles/")
+    out["note"] = ("dense spike output timed with each call (1 B per pixel-step); f1_vs_f32 at "
+                   "delta 0, 1, 2 steps (maximum matching per pixel and polarity, et_spike_matches); "
+                   "EMD is the paper's bidirectional loss (Eq. 8-9) between the two spike trains, mean "
+                   "over pixels; tensor-pipe counters in profiles/")
     del logl
     torch.cuda.empty_cache()
     return out

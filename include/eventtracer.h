@@ -186,8 +186,13 @@ int et_render_annotations(const et_scene* scene, const et_camera* cams, int32_t 
  * ET_RENDER_WAVEFRONT_TILES (default): the wavefront schedule with each warp's
  * primary rays taken from an 8 x 4 pixel tile instead of 32 pixels of one row
  * (when W is a multiple of 8 and the rendered rows of 4; else raster order).
+ * ET_RENDER_WAVEFRONT_SORTED: the tiled schedule with each bounce's
+ * continuation rays sorted by direction cell and origin cell (a stable radix
+ * sort on a 24-bit key) before they are traced; a further ~16 B per path of
+ * workspace, kept like the rest.
  * Errors: ET_ERR_ARG. */
-enum { ET_RENDER_WAVEFRONT = 0, ET_RENDER_MEGAKERNEL = 1, ET_RENDER_WAVEFRONT_TILES = 2 };
+enum { ET_RENDER_WAVEFRONT = 0, ET_RENDER_MEGAKERNEL = 1, ET_RENDER_WAVEFRONT_TILES = 2,
+       ET_RENDER_WAVEFRONT_SORTED = 3 };
 int et_render_set_mode(et_scene* scene, int32_t mode);
 
 /* Per-kernel device time of the wavefront schedule, for measurement (not part
@@ -200,7 +205,8 @@ int et_render_set_mode(et_scene* scene, int32_t mode);
  * the previous read and indexed raygen 0, closest-hit trace 1, shade 2,
  * shadow trace 3, accumulate 4: ms[5] device milliseconds, launches[5], and
  * items[5] = paths generated, rays traced, hits shaded, shadow rays traced and
- * pixel-frames resolved.  ET_ERR_CAPACITY: more than 32768 queue lengths were
+ * pixel-frames resolved (in ET_RENDER_WAVEFRONT_SORTED the shade time holds
+ * the sort of the continuation queue).  ET_ERR_CAPACITY: more than 32768 queue lengths were
  * recorded between reads (the times stay valid, the counts are short). */
 int et_render_profile(et_scene* scene, int32_t enable);
 int et_render_profile_read(et_scene* scene, double* ms, int64_t* launches, int64_t* items);
@@ -420,6 +426,14 @@ int et_adam_step(float* p, const float* g, float* m, float* v, int64_t n, float 
  * Errors: ET_ERR_ARG. */
 int et_event_matches(const et_event* a, int64_t n_a, const et_event* b, int64_t n_b,
                      int32_t delta, int64_t* matches);
+
+/* The same maximum-matching size for two dense spike tensors a, b (device,
+ * int8 [K][npix], values -1 / 0 / +1 as written by et_evsnet_forward's spike
+ * output; the step index is the event time): one thread per pixel, on
+ * `stream`.  *matches (device, one int64) is overwritten when the kernel
+ * completes.  0 <= delta <= 30.  Errors: ET_ERR_ARG, ET_ERR_CUDA. */
+int et_spike_matches(const int8_t* a, const int8_t* b, int64_t K, int64_t npix, int32_t delta,
+                     int64_t* matches, void* stream);
 
 const char* et_status_str(int status);
 

@@ -15,7 +15,7 @@ ET_LAMBERT, ET_GGX = 0, 1
 ET_LOG_EPS, ET_LOG_PAPER = 0, 1
 ET_F32, ET_BF16, ET_FP8 = 0, 1, 2
 ET_NET_STACK, ET_NET_RESIDUAL = 0, 1
-ET_RENDER_WAVEFRONT, ET_RENDER_MEGAKERNEL, ET_RENDER_WAVEFRONT_TILES = 0, 1, 2
+ET_RENDER_WAVEFRONT, ET_RENDER_MEGAKERNEL, ET_RENDER_WAVEFRONT_TILES, ET_RENDER_WAVEFRONT_SORTED = 0, 1, 2, 3
 ET_BVH_GPU, ET_BVH_HOST, ET_BVH_SWEEP, ET_BVH_GPU_SWEEP = 0, 1, 2, 3
 
 
@@ -80,6 +80,7 @@ SIGNATURES = {
     "et_train_static_workspace_capacity": (C.c_size_t, []),
     "et_adam_step": (i32, [P, P, P, P, i64, f32, f32, f32, f32, i32, P]),
     "et_event_matches": (i32, [P, i64, P, i64, i32, P]),
+    "et_spike_matches": (i32, [P, P, i64, i64, i32, P, P]),
     "et_status_str": (C.c_char_p, [i32]),
     "et_kernel_launches": (u64, []),
     "et_sensor_events": (i32, [P, i32, i32, i32, P, i32, P, i32, P, i64, P, P]),

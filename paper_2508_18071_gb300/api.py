@@ -79,7 +79,8 @@ class Scene:
                                                              _stream(stream)))
 
     def set_mode(self, mode: int):
-        """ET_RENDER_WAVEFRONT_TILES (default), ET_RENDER_WAVEFRONT or ET_RENDER_MEGAKERNEL."""
+        """ET_RENDER_WAVEFRONT_TILES (default), ET_RENDER_WAVEFRONT_SORTED, ET_RENDER_WAVEFRONT or
+        ET_RENDER_MEGAKERNEL."""
         L.check("et_render_set_mode", L.load().et_render_set_mode(self._h, int(mode)))
 
     PROFILE_KINDS = ("raygen", "trace", "shade", "shadow", "accumulate")
@@ -270,6 +271,22 @@ def event_f1(pred: np.ndarray, ref: np.ndarray, delta: int) -> float:
                                    nb, int(delta), C.byref(m))
     L.check("et_event_matches", st)
     return 2.0 * m.value / (na + nb)
+
+
+def spike_f1(a: torch.Tensor, b: torch.Tensor, delta: int, stream=None) -> float:
+    """Event F1 of two dense spike tensors (device int8 [K, H, W] of -1 / 0 / +1)
+    via et_spike_matches; both silent -> 1."""
+    assert a.shape == b.shape and a.dtype == torch.int8 and b.dtype == torch.int8
+    a, b = a.contiguous(), b.contiguous()
+    na, nb = int((a != 0).sum().item()), int((b != 0).sum().item())
+    if na + nb == 0:
+        return 1.0
+    m = torch.zeros(1, dtype=torch.int64, device=a.device)
+    K = a.shape[0]
+    st = L.load().et_spike_matches(_ptr(a), _ptr(b), K, a.numel() // max(K, 1), int(delta), _ptr(m),
+                                   _stream(stream))
+    L.check("et_spike_matches", st)
+    return 2.0 * int(m.item()) / (na + nb)
 
 
 # ------------------------------------------------------------ sensor model

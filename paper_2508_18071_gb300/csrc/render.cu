@@ -206,7 +206,7 @@ extern "C" int et_render_profile_read(et_scene* scene, double* ms, int64_t* laun
 
 extern "C" int et_render_set_mode(et_scene* scene, int32_t mode) {
   if (!scene || (mode != ET_RENDER_WAVEFRONT && mode != ET_RENDER_MEGAKERNEL &&
-                 mode != ET_RENDER_WAVEFRONT_TILES))
+                 mode != ET_RENDER_WAVEFRONT_TILES && mode != ET_RENDER_WAVEFRONT_SORTED))
     return ET_ERR_ARG;
   scene->render_mode = mode;
   return ET_OK;

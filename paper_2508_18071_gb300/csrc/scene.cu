@@ -286,6 +286,7 @@ extern "C" int et_build_scene_with(const float* tris, const uint32_t* tri_mat, i
   std::vector<int32_t> slot_tri((size_t)std::max<int64_t>(n, 1), 0);   // leaf slot -> input triangle
   std::vector<int> refit_order, refit_levels{0};                        // inner nodes, deepest level first
   int root_ref = -1;   // an empty leaf: first 0, count 0
+  float box_lo[3] = {0, 0, 0}, box_hi[3] = {0, 0, 0};
   double sah = 0.0;
   int64_t n_nodes = 0;
   int builder = builder_req;
@@ -340,6 +341,7 @@ extern "C" int et_build_scene_with(const float* tris, const uint32_t* tri_mat, i
     }
     n_nodes = (int64_t)bn.size();
     root_ref = ref_of(bn, inner_index, 0);
+    for (int k = 0; k < 3; ++k) { box_lo[k] = bn[0].box.lo[k]; box_hi[k] = bn[0].box.hi[k]; }
     {
       // refit schedule: inner nodes by depth, deepest first
       std::vector<std::vector<int>> by_depth;
@@ -385,6 +387,7 @@ extern "C" int et_build_scene_with(const float* tris, const uint32_t* tri_mat, i
   s->n_tris = n; s->n_nodes = n_nodes; s->sah = sah; s->builder = builder;
   s->n_user = n_tris;
   s->refit_levels = refit_levels;
+  for (int k = 0; k < 3; ++k) { s->box_lo[k] = box_lo[k]; s->box_hi[k] = box_hi[k]; }
   auto fail = [&](int code) { et_scene_free(s); return code; };
   cudaError_t e;
 #define ET_SCENE_ALLOC(ptr, bytes)                                   \
@@ -429,6 +432,7 @@ extern "C" void et_scene_free(et_scene* s) {
   cudaFree(s->d_tris); cudaFree(s->d_nodes); cudaFree(s->d_mats); cudaFree(s->d_lights);
   cudaFree(s->d_cams);
   cudaFree(s->wf_mem);
+  cudaFree(s->wf_sort_mem);
   cudaFree(s->d_perm);
   cudaFree(s->d_refit);
   cudaFree(s->d_upd);

@@ -33,6 +33,10 @@ struct et_scene {
   int builder = ET_BVH_GPU;
   void* wf_mem = nullptr;        // wavefront queues and path state, grown on demand
   int64_t wf_cap = 0, wf_acc_cap = 0;
+  void* wf_sort_mem = nullptr;   // sorted mode: keys, indices and radix-sort scratch
+  int64_t wf_sort_cap = 0;
+  size_t wf_sort_tmp = 0;
+  float box_lo[3] = {0, 0, 0}, box_hi[3] = {0, 0, 0};   // the hierarchy's root box
   // moving geometry (et_scene_update): leaf slot -> input triangle, inner nodes
   // deepest level first with the level boundaries, upload staging
   int64_t n_user = 0;

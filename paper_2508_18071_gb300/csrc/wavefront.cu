@@ -16,6 +16,7 @@
 // (the same order as the one-kernel schedule) and writes RGB and Eq. 1 log
 // luminance.  Queues are compacted with one atomic per warp.
 #include <algorithm>
+#include <cub/device/device_radix_sort.cuh>
 #include "et_internal.cuh"
 #include "pt_common.cuh"
 #include "scene_internal.h"
@@ -54,6 +55,49 @@ __host__ __device__ __forceinline__ int64_t slot_pixel(const Batch& bt, int64_t 
   return (ty * 4 + ((i >> 3) & 3)) * bt.W + tx * 8 + (i & 7);
 }
 
+// Extension rays reordered between bounces (ET_RENDER_WAVEFRONT_SORTED): the
+// shading kernel writes a 24-bit key for every continuation ray it appends,
+// the queue is sorted by key (stable radix sort) and the next closest-hit
+// trace takes its rays through the sorted permutation.  Key: the direction's
+// cell on an 8 x 8 octahedral map above (or below) a Morton code of the
+// origin's cell on a 64^3 grid over the scene's box.  The order of a queue
+// changes no path's arithmetic.
+#ifndef ET_SORT_DIR_MAJOR
+#define ET_SORT_DIR_MAJOR 1
+#endif
+constexpr int kSortBits = 24;
+
+struct SortBox { float lo[3], scale[3]; };
+
+__host__ __device__ __forceinline__ uint32_t spread3(uint32_t v) {   // 6 bits -> every third bit
+  v &= 0x3Fu;
+  v = (v | (v << 8)) & 0x0300F00Fu;
+  v = (v | (v << 4)) & 0x030C30C3u;
+  v = (v | (v << 2)) & 0x09249249u;
+  return v;
+}
+
+__device__ __forceinline__ uint32_t ray_key(const SortBox& B, f3 o, f3 d) {
+  const float sx = fabsf(d.x) + fabsf(d.y) + fabsf(d.z);
+  float u = d.x / sx, v = d.y / sx;
+  if (d.z < 0.0f) {
+    const float uu = (1.0f - fabsf(v)) * (u < 0.0f ? -1.0f : 1.0f);
+    v = (1.0f - fabsf(u)) * (v < 0.0f ? -1.0f : 1.0f);
+    u = uu;
+  }
+  const uint32_t du = (uint32_t)min(7, max(0, (int)((u + 1.0f) * 4.0f)));
+  const uint32_t dv = (uint32_t)min(7, max(0, (int)((v + 1.0f) * 4.0f)));
+  const uint32_t dir = (dv << 3) | du;
+  const float c[3] = {o.x, o.y, o.z};
+  uint32_t m = 0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int q = (int)((c[k] - B.lo[k]) * B.scale[k]);
+    m |= spread3((uint32_t)min(63, max(0, q))) << k;
+  }
+  return ET_SORT_DIR_MAJOR ? (dir << 18) | m : (m << 6) | dir;
+}
+
 struct Args {
   et_scene_dev S;
   const et_camera* cams;
@@ -71,6 +115,10 @@ struct Args {
   float4* shc;
   uint32_t* ctr;
   int32_t* records;
+  uint32_t* skey;       // sorted mode: keys and queue indices the shading kernel appends
+  uint32_t* sval;
+  const uint32_t* perm; // sorted mode: queue index of the i-th ray the trace takes
+  SortBox box;
 };
 
 // path q of the batch -> (frame of the call, sample, pixel)
@@ -144,7 +192,10 @@ __global__ void __launch_bounds__(128, ET_TRACE_MIN_BLOCKS) wf_trace(Args A, int
           idx = (int)my;
           float4 o, d;
           if (kShadow) { o = A.sho[my]; d = A.shd[my]; }
-          else { o = A.qo[cur][my]; d = A.qd[cur][my]; }
+          else {
+            if (A.perm) idx = (int)A.perm[my];
+            o = A.qo[cur][idx]; d = A.qd[cur][idx];
+          }
           pt::ray_setup(ray, mk(o.x, o.y, o.z), mk(d.x, d.y, d.z));
           tr.start(A.S, kShadow ? d.w : FLT_MAX);
         } else {
@@ -251,6 +302,10 @@ __global__ void __launch_bounds__(256) wf_shade(Args A, int cur, int b) {
     if (want_ray) {
       A.qo[nxt][jr] = make_float4(v.on.x, v.on.y, v.on.z, __uint_as_float(q));
       A.qd[nxt][jr] = make_float4(d_next.x, d_next.y, d_next.z, 0.0f);
+      if (A.skey) {
+        A.skey[jr] = ray_key(A.box, v.on, d_next);
+        A.sval[jr] = jr;
+      }
     }
   }
 }
@@ -290,6 +345,34 @@ int ensure_workspace(et_scene* s, int64_t paths, int64_t acc_pix) {
   return ET_OK;
 }
 
+// keys, key copies, indices and the permutation (4 x 4 B per path) plus the
+// radix sort's scratch, grown on demand
+int ensure_sort_workspace(et_scene* s, int64_t paths, uint32_t** key, uint32_t** key_alt, uint32_t** val,
+                          uint32_t** perm, void** tmp, size_t* tmp_bytes) {
+  if (s->wf_sort_cap < paths) {
+    cudaFree(s->wf_sort_mem);
+    s->wf_sort_mem = nullptr;
+    s->wf_sort_cap = 0;
+    size_t tb = 0;
+    ET_CHECK_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tb, (const uint32_t*)nullptr, (uint32_t*)nullptr,
+                                                  (const uint32_t*)nullptr, (uint32_t*)nullptr,
+                                                  (int)paths, 0, kSortBits));
+    tb = (tb + 255) & ~(size_t)255;
+    ET_CHECK_CUDA(cudaMalloc(&s->wf_sort_mem, (size_t)paths * 16 + tb));
+    s->wf_sort_cap = paths;
+    s->wf_sort_tmp = tb;
+  }
+  char* p = static_cast<char*>(s->wf_sort_mem);
+  const int64_t cap = s->wf_sort_cap;
+  *tmp = p; p += s->wf_sort_tmp;
+  *tmp_bytes = s->wf_sort_tmp;
+  *key = reinterpret_cast<uint32_t*>(p); p += 4 * cap;
+  *key_alt = reinterpret_cast<uint32_t*>(p); p += 4 * cap;
+  *val = reinterpret_cast<uint32_t*>(p); p += 4 * cap;
+  *perm = reinterpret_cast<uint32_t*>(p);
+  return ET_OK;
+}
+
 }  // namespace
 
 int et_render_wavefront(et_scene* s, int n_frames, int first_frame, int W, int H, int y0, int y1,
@@ -300,7 +383,8 @@ int et_render_wavefront(et_scene* s, int n_frames, int first_frame, int W, int H
   Batch proto{};
   proto.npix = npix;
   proto.W = W;
-  proto.tiled = s->render_mode == ET_RENDER_WAVEFRONT_TILES && W % 8 == 0 && (y1 - y0) % 4 == 0;
+  proto.tiled = (s->render_mode == ET_RENDER_WAVEFRONT_TILES || s->render_mode == ET_RENDER_WAVEFRONT_SORTED) &&
+                W % 8 == 0 && (y1 - y0) % 4 == 0;
   int frames_per_batch, samples_per_batch;
   if (spp <= planes) {
     samples_per_batch = spp;
@@ -339,6 +423,18 @@ int et_render_wavefront(et_scene* s, int n_frames, int first_frame, int W, int H
   ET_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_c, wf_trace<false>, 128, 0));
   ET_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_s, wf_trace<true>, 128, 0));
   const int grid_c = nsm * std::max(occ_c, 1), grid_s = nsm * std::max(occ_s, 1);
+  const bool sorted = s->render_mode == ET_RENDER_WAVEFRONT_SORTED && max_depth > 1;
+  uint32_t *skey = nullptr, *skey_alt = nullptr, *sval = nullptr, *sperm = nullptr;
+  void* stmp = nullptr;
+  size_t stmp_bytes = 0;
+  if (sorted) {
+    ET_TRY(ensure_sort_workspace(s, cap, &skey, &skey_alt, &sval, &sperm, &stmp, &stmp_bytes));
+    for (int k = 0; k < 3; ++k) {
+      const float ext = s->box_hi[k] - s->box_lo[k];
+      A.box.lo[k] = s->box_lo[k];
+      A.box.scale[k] = ext > 0.0f ? 64.0f / ext : 0.0f;
+    }
+  }
   const int grid_shade = nsm * 8;
   for (int f0 = 0; f0 < n_frames; f0 += frames_per_batch) {
     const int nf = std::min(frames_per_batch, n_frames - f0);
@@ -358,13 +454,28 @@ int et_render_wavefront(et_scene* s, int n_frames, int first_frame, int W, int H
         const int nxt = cur ^ 1;
         ET_CHECK_CUDA(cudaMemsetAsync(A.ctr + C_NRAY0 + nxt, 0, sizeof(uint32_t), stream));
         ET_CHECK_CUDA(cudaMemsetAsync(A.ctr + C_NSH, 0, sizeof(uint32_t) * 3, stream));
+        const bool sort_next = sorted && b < max_depth;
+        Args At = A, Ash = A;
+        At.perm = sorted && b > 1 ? sperm : nullptr;
+        if (sort_next) {
+          Ash.skey = skey;
+          Ash.sval = sval;
+          ET_CHECK_CUDA(cudaMemsetAsync(skey, 0xFF, sizeof(uint32_t) * bt.paths, stream));
+        }
         ET_TRY(prof_begin(s, kProfTrace, stream, &pe));
-        wf_trace<false><<<grid_c, 128, 0, stream>>>(A, cur, b);
+        wf_trace<false><<<grid_c, 128, 0, stream>>>(At, cur, b);
         ET_CHECK_LAUNCH();
         ET_TRY(prof_end(s, kProfTrace, pe, 0, A.ctr + C_NRAY0 + cur, stream));
         ET_TRY(prof_begin(s, kProfShade, stream, &pe));
-        wf_shade<<<grid_shade, 256, 0, stream>>>(A, cur, b);
+        wf_shade<<<grid_shade, 256, 0, stream>>>(Ash, cur, b);
         ET_CHECK_LAUNCH();
+        if (sort_next) {
+          // the continuation queue's live entries hold keys below or equal to
+          // the all-ones filler of the rest, and the sort is stable: the
+          // first n entries of the permutation are the queue's n rays
+          ET_CHECK_CUDA(cub::DeviceRadixSort::SortPairs(stmp, stmp_bytes, skey, skey_alt, sval, sperm,
+                                                        (int)bt.paths, 0, kSortBits, stream));
+        }
         ET_TRY(prof_end(s, kProfShade, pe, 0, A.ctr + C_NRAY0 + cur, stream));
         if (s->dev.n_lights > 0 && b < max_depth) {
           ET_TRY(prof_begin(s, kProfShadow, stream, &pe));

@@ -2,8 +2,9 @@
 1 SPP, 2000 frames by default) through the EvSNet convolutions in FP32, BF16
 and FP8 (E4M3 with power-of-two scales, FP32 accumulation), reporting per
 precision the device time, throughput, event count, event F1 against the FP32
-output (matching per pixel and step, delta = 0) and the bidirectional EMD to
-the FP32 output (the paper's Eq. 8-9, averaged over pixels).
+output (maximum matching per pixel and polarity with the step difference at
+most delta = 0, 1, 2) and the bidirectional EMD to the FP32 output (the
+paper's Eq. 8-9, averaged over pixels).
 
     python -m paper_2508_18071_gb300.precision_sweep [--frames 2000] [--spp 1]
 
@@ -72,9 +73,7 @@ def sweep(logl: torch.Tensor, net_d: dict, cap=1 << 20) -> dict:
         n = int((S != 0).sum().item())
         if ref is None:
             ref = S
-        match = int(((S == ref) & (S != 0)).sum().item())
-        n_ref = int((ref != 0).sum().item())
-        f1 = 1.0 if n + n_ref == 0 else 2.0 * match / (n + n_ref)
+        f1 = [api.spike_f1(S, ref, dl) for dl in (0, 1, 2)]
         loss, _, _ = training.emd_count_loss(S.unsqueeze(0), ref.unsqueeze(0).float(), 0.0)
         out[name] = {"ms_per_frame": ms / K, "tflops": flops / (ms / 1e3) / 1e12, "events": n,
                      "f1_vs_f32": f1, "emd_vs_f32": float(loss[1].item())}

@@ -82,18 +82,21 @@ def test_wavefront_no_lights_and_empty_scene(api):
 @pytest.mark.parametrize("W,H", [(64, 48), (1280, 720), (45, 37)])
 def test_tile_order_equals_raster_order(api, W, H):
     """The default wavefront takes each warp's primary rays from an 8 x 4 pixel
-    tile: only the order in which paths sit in the queues changes, so every
-    output is bit for bit the raster-order one (ragged sizes fall back to
-    raster order)."""
+    tile, and the sorted mode also reorders every bounce's continuation rays by
+    direction and origin cell: only the order in which paths sit in the queues
+    changes, so every output is bit for bit the raster-order one (ragged sizes
+    fall back to raster order)."""
     from paper_2508_18071_gb300 import _lib
     s = inputs.random_scene(seed=11) if W < 100 else inputs.city_block(seed=21)
     cams = inputs.random_scene_path(2, first=5) if W < 100 else inputs.city_path(2, first=200)
     g = api.Scene(s)
     outs = []
-    for mode in (_lib.ET_RENDER_WAVEFRONT_TILES, _lib.ET_RENDER_WAVEFRONT):
+    for mode in (_lib.ET_RENDER_WAVEFRONT, _lib.ET_RENDER_WAVEFRONT_TILES, _lib.ET_RENDER_WAVEFRONT_SORTED):
         g.set_mode(mode)
         rgb, logl, rec = api.render_frames(g, cams, W, H, 2, 5, 17, first_frame=5, records=W < 100)
         outs.append((rgb.cpu().numpy(), logl.cpu().numpy(), None if rec is None else rec.cpu().numpy()))
-    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
-    if outs[0][2] is not None:
-        assert np.array_equal(outs[0][2], outs[1][2])
+    assert np.abs(outs[0][1]).max() > 0
+    for o in outs[1:]:
+        assert np.array_equal(o[0], outs[0][0]) and np.array_equal(o[1], outs[0][1])
+        if o[2] is not None:
+            assert np.array_equal(o[2], outs[0][2])
