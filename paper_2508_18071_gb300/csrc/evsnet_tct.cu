@@ -13,11 +13,15 @@
 // (its last kt inputs) lives in shared memory as a ring of kt + kT - 1 slots,
 // each slot one step of 128 pixels x 16 channels in the K-major, no-swizzle
 // operand layout (two 2 KB planes of 8 channels, 16-byte rows), so the A
-// operand of tap tau is simply the slot of step s - (kt - 1) + tau: a layer's
-// output for kT consecutive steps is kT x kt MMAs of M = 128, N = 16, K = 16,
-// accumulated in kT groups of 16 TMEM columns.  One step of a layer therefore
-// costs one MMA round trip (issue, commit, mbarrier wait, tcgen05.ld) per kT
-// steps; the epilogue (bias, ReLU, residual add, BF16 rounding) writes the
+// operand of tap tau is simply the slot of step s - (kt - 1) + tau.  The kT = 2
+// steps of a round trip read kt + 1 slots; slot i feeds output step j through
+// tap i - j, so one MMA per slot with N = 32 computes both steps' shares at
+// once: its B operand is the window [W_i ; W_(i-1)] of the layer's taps stored
+// in descending order as one strip (rows W_(kt-1), ..., W_0), and only the
+// first and last slot, which feed one step each, take N = 16 MMAs.  A layer's
+// two steps are kt + 1 MMAs (M = 128, K = 16) instead of 2 kt, accumulated in
+// two groups of 16 TMEM columns.  One step of a layer costs one MMA round trip
+// (issue, commit, mbarrier wait, tcgen05.ld) per kT steps; the epilogue (bias, ReLU, residual add, BF16 rounding) writes the
 // next layer's ring slot, or, after the last layer, feeds the projection and
 // BiLIF.  The caller's FP32 history state ([layer][kt-1][C][H][W]) is read
 // into the rings at the start and written back at the end; values written
@@ -47,7 +51,8 @@ namespace {
 
 constexpr int TP = 128;                 // pixels per tile = MMA M = TMEM lanes
 constexpr int CP = 16;                  // channels (C <= 16, zero-padded)
-constexpr int kT = 2;                   // steps per MMA round trip
+constexpr int kT = 2;                   // steps per MMA round trip (the MMA schedule assumes 2)
+static_assert(kT == 2, "one N = 32 MMA per middle slot covers exactly two steps");
 constexpr int kMaxKt = 7;
 constexpr int kMaxStem = 7;
 constexpr int kSlot = TP * CP * 2;      // bytes of one ring slot
@@ -152,24 +157,29 @@ evsnet_tct_kernel(const __grid_constant__ CUtensorMap tmap, TctParams P, const f
     const int t = i / CP, c = i % CP;
     w0[i] = c < C ? wg[c * taps0 + t] : 0.0f;                 // layer 0: [C][1][taps]
   }
-  // B operands: layer l >= 1, tap tau: rows n (output channel), K = input
-  // channel in two planes of 8
+  // B operands: one strip per layer l >= 1 of kt blocks of 16 rows, block b
+  // holding tap kt - 1 - b (rows n = output channel, K = input channel in two
+  // planes of 8, each plane kt x 16 rows of 16 bytes)
   for (int i = tid; i < (L - 1) * kt * CP * CP; i += kThreads) {
     const int k = i % CP, n = (i / CP) % CP, tau = (i / (CP * CP)) % kt, l = 1 + i / (CP * CP * kt);
     float v = 0.0f;
     if (n < C && k < C) v = wg[P.woff[l] + (n * C + k) * kt + tau];
-    unsigned char* dst = wB + ((size_t)(l - 1) * kt + tau) * (CP * CP * 2) + (k >> 3) * (CP * 16) + n * 16 +
-                         (k & 7) * 2;
+    unsigned char* dst = wB + (size_t)(l - 1) * kt * (CP * CP * 2) + (k >> 3) * (kt * CP * 16) +
+                         ((kt - 1 - tau) * CP + n) * 16 + (k & 7) * 2;
     *reinterpret_cast<__nv_bfloat16*>(dst) = __float2bfloat16_rn(v);
   }
-  // ring slots of steps -(kt-1) .. -1 from the state (oldest first)
+  // ring slots of steps -(kt-1) .. -1 from the state (oldest first); a
+  // layer's loads are all issued before its stores
   for (int l = 1; l < L; ++l) {
-    for (int j = 0; j < hk; ++j) {
-      float v[kHalf];
+    float v[kMaxKt - 1][kHalf];
 #pragma unroll
-      for (int c = 0; c < kHalf; ++c) v[c] = (live && c0 + c < C) ? hist[hidx(l, j, c0 + c)] : 0.0f;
-      store_half(slot_of(l, ring_pos(j - hk, R)), hc, p, v);
-    }
+    for (int j = 0; j < kMaxKt - 1; ++j)
+#pragma unroll
+      for (int c = 0; c < kHalf; ++c)
+        v[j][c] = (j < hk && live && c0 + c < C) ? hist[hidx(l, j, c0 + c)] : 0.0f;
+#pragma unroll
+    for (int j = 0; j < kMaxKt - 1; ++j)
+      if (j < hk) store_half(slot_of(l, ring_pos(j - hk, R)), hc, p, v[j]);
   }
   if (ks0 == 0) {
     // both halves write the same values: each reads back its own writes
@@ -183,9 +193,9 @@ evsnet_tct_kernel(const __grid_constant__ CUtensorMap tmap, TctParams P, const f
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
   const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
-  const uint32_t idesc = umma_idesc_bf16(TP, CP);
+  const uint32_t idesc16 = umma_idesc_bf16(TP, CP), idesc32 = umma_idesc_bf16(TP, 2 * CP);
   const uint64_t a_desc0 = umma_desc(smem_u32(rings), kPlane, 128);
-  const uint64_t b_desc0 = umma_desc(smem_u32(wB), CP * 16, 128);
+  const uint64_t b_desc0 = umma_desc(smem_u32(wB), kt * CP * 16, 128);
   uint32_t phase = 0;
 
   const int S = P.F - P.f0;             // steps of this call
@@ -304,14 +314,17 @@ evsnet_tct_kernel(const __grid_constant__ CUtensorMap tmap, TctParams P, const f
         // slots are 4 KB apart, B blocks 512 B
         const uint64_t a0 = a_desc0 + (uint64_t)((l - 1) * R) * (kSlot >> 4);
         const uint64_t b0 = b_desc0 + (uint64_t)((l - 1) * kt) * ((CP * CP * 2) >> 4);
+        constexpr uint64_t kBlock = (CP * 16) >> 4;   // one 16-row block of the strip
         const int p0 = ring_pos(s0 - hk, R);
-        for (int j = 0; j < tc; ++j)
-          for (int tau = 0; tau < kt; ++tau) {
-            int pos = p0 + j + tau;
-            pos = pos >= R ? pos - R : pos;
-            umma_bf16(tmem + j * CP, a0 + (uint64_t)pos * (kSlot >> 4),
-                      b0 + (uint64_t)tau * ((CP * CP * 2) >> 4), idesc, tau != 0);
-          }
+        auto a_of = [&](int i) {
+          const int pos = p0 + i >= R ? p0 + i - R : p0 + i;
+          return a0 + (uint64_t)pos * (kSlot >> 4);
+        };
+        // slot 0 starts step 0 (tap 0), slot kt starts step 1 (tap kt - 1);
+        // slots 1 .. kt - 1 add to both (taps i and i - 1)
+        umma_bf16(tmem, a_of(0), b0 + (uint64_t)(kt - 1) * kBlock, idesc16, 0);
+        if (tc > 1) umma_bf16(tmem + CP, a_of(kt), b0, idesc16, 0);
+        for (int i = 1; i < kt; ++i) umma_bf16(tmem, a_of(i), b0 + (uint64_t)(kt - 1 - i) * kBlock, idesc32, 1);
         umma_commit(&mma_bar);
       }
       const bool ok = mbar_wait(&mma_bar, phase, P.wait_iters);
@@ -325,11 +338,13 @@ evsnet_tct_kernel(const __grid_constant__ CUtensorMap tmap, TctParams P, const f
       if (bail) break;
       const bool closing = P.kind == ET_NET_RESIDUAL && (l % 2) == 0;
       const bool inner = P.kind == ET_NET_RESIDUAL && (l % 2) == 1;
+      // both steps' accumulators (the second is unused when tc == 1)
+      float accs[kT][kHalf];
+      tmem_ld8x2(tmem + lane_base + c0, tmem + lane_base + CP + c0, accs[0], accs[1]);
 #pragma unroll
       for (int j = 0; j < kT; ++j) {
         if (j >= tc) break;
-        float acc[kHalf];
-        tmem_ld8(tmem + lane_base + j * CP + c0, acc);
+        const float* acc = accs[j];
         float out[kHalf];
 #pragma unroll
         for (int c = 0; c < kHalf; ++c) {
