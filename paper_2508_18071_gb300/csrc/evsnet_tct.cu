@@ -8,25 +8,35 @@
 // A CTA owns a tile of 128 consecutive pixels for the whole call: one TMEM
 // lane per pixel and two threads per pixel (warps w and w + 4 share TMEM lane
 // quarter w), each owning 8 of the 16 channels -- its 8 accumulator columns,
-// one 16-byte plane row of the operands and half of every epilogue -- so that
-// two warps per scheduler hide each other's latencies.  The input history of every layer >= 1
-// (its last kt inputs) lives in shared memory as a ring of kt + kT - 1 slots,
-// each slot one step of 128 pixels x 16 channels in the K-major, no-swizzle
-// operand layout (two 2 KB planes of 8 channels, 16-byte rows), so the A
-// operand of tap tau is simply the slot of step s - (kt - 1) + tau.  The kT = 2
-// steps of a round trip read kt + 1 slots; slot i feeds output step j through
-// tap i - j, so one MMA per slot with N = 32 computes both steps' shares at
-// once: its B operand is the window [W_i ; W_(i-1)] of the layer's taps stored
-// in descending order as one strip (rows W_(kt-1), ..., W_0), and only the
-// first and last slot, which feed one step each, take N = 16 MMAs.  A layer's
-// two steps are kt + 1 MMAs (M = 128, K = 16) instead of 2 kt, accumulated in
-// two groups of 16 TMEM columns.  One step of a layer costs one MMA round trip
-// (issue, commit, mbarrier wait, tcgen05.ld) per kT steps; the epilogue (bias, ReLU, residual add, BF16 rounding) writes the
-// next layer's ring slot, or, after the last layer, feeds the projection and
-// BiLIF.  The caller's FP32 history state ([layer][kt-1][C][H][W]) is read
-// into the rings at the start and written back at the end; values written
-// by this kernel are BF16-rounded, so a later call of the BF16 path reads them
-// back exactly.
+// one 16-byte plane row of the operands and half of every epilogue -- plus a
+// ninth warp whose one thread issues every MMA and TMA copy, so that issuing
+// never holds up the epilogues.  The input history of every layer >= 1 (its
+// last kt inputs) lives in shared memory as a ring of kt + kT - 1 slots, each
+// slot one step of 128 pixels x 16 channels in the K-major, no-swizzle operand
+// layout (two 2 KB planes of 8 channels, 16-byte rows), so the A operand of tap
+// tau is simply the slot of step s - (kt - 1) + tau.  The kT = 2 steps of a
+// chunk read kt + 1 slots; slot i feeds output step j through tap i - j, so
+// one MMA per slot with N = 32 computes both steps' shares at once: its B
+// operand is the window [W_i ; W_(i-1)] of the layer's taps stored in
+// descending order as one strip (rows W_(kt-1), ..., W_0), and only the first
+// and last slot, which feed one step each, take N = 16 MMAs.  A layer's two
+// steps are kt + 1 MMAs (M = 128, K = 16), accumulated in two groups of 16
+// TMEM columns.
+//
+// The layers run as a wavefront over chunks: in round tau, layer 0 (CUDA
+// cores) computes chunk tau and tensor-core layer l chunk tau - l + 1.  One
+// barrier per round makes the rings' new slots visible to the tensor core;
+// the issuing thread then issues every layer's MMAs, last layer first, with
+// one commit per layer, and the pixel warps run each layer's epilogue as soon
+// as its commit arrives (bias, ReLU, residual add, BF16 rounding into the next
+// layer's ring; after the last layer the projection and BiLIF).  Layer l's
+// epilogue overwrites slots that layer l + 1's MMAs of the same round read;
+// those were issued earlier, and a commit covers every earlier MMA.  The FP32
+// input of each residual block waits for its closing layer in TMEM (two
+// chunks per block).  The caller's FP32 history state ([layer][kt-1][C][H][W])
+// is read into the rings at the start and written back at the end; values
+// written by this kernel are BF16-rounded, so a later call of the BF16 path
+// reads them back exactly.
 //
 // The 3 x 3 stem's input: when the image width is a multiple of 128 (a tile is
 // then one row segment), each chunk's log frames f - 1 .. f + 1, rows y - 1 ..
@@ -58,8 +68,14 @@ constexpr int kMaxStem = 7;
 constexpr int kSlot = TP * CP * 2;      // bytes of one ring slot
 constexpr int kPlane = TP * 16;         // bytes of 8 channels of 128 rows
 constexpr int kHalf = CP / 2;            // channels per thread
-constexpr int kThreads = 2 * TP;
-constexpr uint32_t kTmemCols = 32;      // kT x 16 accumulator columns
+constexpr int kWorkers = 2 * TP;       // two threads per pixel
+constexpr int kThreads = kWorkers + 32; // and one warp that issues the MMAs and the TMA copies
+constexpr int kIssuer = kWorkers;       // its issuing thread
+// TMEM: kT x 16 accumulator columns per tensor-core layer, then the FP32
+// block inputs of up to three residual blocks for two chunks
+constexpr int kHbCol = (kMaxLayers - 1) * kT * 16;
+constexpr uint32_t kTmemCols = 512;
+static_assert(kHbCol + 3 * 2 * kT * 16 <= (int)kTmemCols, "TMEM columns");
 constexpr unsigned long long kTimeoutBit = 1ull << 62;
 constexpr uint32_t kDrainIters = 1u << 22;   // bound of the waits for work in flight after a bail
 
@@ -80,6 +96,9 @@ constexpr int kBoxFloats = kBoxW * 3 * 3;
 constexpr uint32_t kBoxBytes = kBoxFloats * 4;
 
 __device__ __forceinline__ int ring_pos(int s, int R) { return ((s % R) + R) % R; }
+
+// barrier of the pixel warps only (the issuing warp does not take part)
+__device__ __forceinline__ void workers_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kWorkers) : "memory"); }
 
 // two floats as one 32-bit word of BF16 (round to nearest even), low half first
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
@@ -118,8 +137,9 @@ evsnet_tct_kernel(const __grid_constant__ CUtensorMap tmap, TctParams P, const f
                   unsigned long long* n_events, float* __restrict__ I_out,
                   int8_t* __restrict__ spikes) {
   extern __shared__ __align__(1024) unsigned char sm[];
-  __shared__ uint64_t mma_bar;
+  __shared__ uint64_t lbar[kMaxLayers];  // commit of tensor-core layer l's MMAs in a round
   __shared__ uint64_t tma_bar;
+  __shared__ uint64_t drain_bar;
   __shared__ uint32_t tmem_slot;
   __shared__ int bail;
   __shared__ float part[kT][TP];        // the second half's share of the projection
@@ -130,7 +150,8 @@ evsnet_tct_kernel(const __grid_constant__ CUtensorMap tmap, TctParams P, const f
   const int c0 = hc * kHalf;
   const int64_t npix = (int64_t)P.H * P.W;
   const int64_t q = (int64_t)blockIdx.x * TP + p;
-  const bool live = q < npix;
+  const bool worker = tid < kWorkers;
+  const bool live = worker && q < npix;
   const int px = live ? (int)(q % P.W) : 0, py = live ? (int)(q / P.W) : 0;
   unsigned char* rings = sm;                                   // [L-1][R] slots
   unsigned char* wB = sm + P.off_wB;                           // [L-1][kt] 16 x 16 BF16
@@ -179,15 +200,20 @@ evsnet_tct_kernel(const __grid_constant__ CUtensorMap tmap, TctParams P, const f
         v[j][c] = (j < hk && live && c0 + c < C) ? hist[hidx(l, j, c0 + c)] : 0.0f;
 #pragma unroll
     for (int j = 0; j < kMaxKt - 1; ++j)
-      if (j < hk) store_half(slot_of(l, ring_pos(j - hk, R)), hc, p, v[j]);
+      if (worker && j < hk) store_half(slot_of(l, ring_pos(j - hk, R)), hc, p, v[j]);
   }
-  if (ks0 == 0) {
+  if (ks0 == 0 && worker) {
     // both halves write the same values: each reads back its own writes
     for (int j = 0; j < hk; ++j) xh[ring_pos(j - hk, R) * TP + p] = live ? hist[hidx(0, j, 0)] : 0.0f;
   }
   float V = (live && hc == 0) ? Vg[q] : 0.0f;
   if (warp == 0) tmem_alloc(&tmem_slot, kTmemCols);
-  if (tid == 0) { mbar_init(&mma_bar, 1); mbar_init(&tma_bar, 1); bail = 0; }
+  if (tid == 0) {
+    for (int l = 0; l < kMaxLayers; ++l) mbar_init(&lbar[l], 1);
+    mbar_init(&tma_bar, 1);
+    mbar_init(&drain_bar, 1);
+    bail = 0;
+  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -196,9 +222,15 @@ evsnet_tct_kernel(const __grid_constant__ CUtensorMap tmap, TctParams P, const f
   const uint32_t idesc16 = umma_idesc_bf16(TP, CP), idesc32 = umma_idesc_bf16(TP, 2 * CP);
   const uint64_t a_desc0 = umma_desc(smem_u32(rings), kPlane, 128);
   const uint64_t b_desc0 = umma_desc(smem_u32(wB), kt * CP * 16, 128);
-  uint32_t phase = 0;
+  // TMEM columns: layer l's accumulators at 32 (l - 1); the FP32 block inputs
+  // of the residual form (block b, chunk parity) at kHbCol + 32 (2 b + parity)
+  auto acc_col = [&](int l) { return tmem + lane_base + (uint32_t)((l - 1) * kT * CP + c0); };
+  auto hb_col = [&](int b, int par) { return tmem + lane_base + (uint32_t)(kHbCol + (2 * b + par) * kT * CP + c0); };
+  uint32_t lphase = 0;                  // bit l: parity of the next completion of lbar[l]
+  const bool residual = P.kind == ET_NET_RESIDUAL;
 
   const int S = P.F - P.f0;             // steps of this call
+  const int nch = (S + kT - 1) / kT;    // chunks of kT steps
   // 3 x 3 stem: the nine neighbours' X of the steps of a chunk, loaded one
   // chunk ahead so that their latency hides behind the tensor-core layers
   float xn[kT][9];
@@ -223,187 +255,212 @@ evsnet_tct_kernel(const __grid_constant__ CUtensorMap tmap, TctParams P, const f
   const int tx0 = (int)(((int64_t)blockIdx.x * TP) % P.W), ty0 = (int)(((int64_t)blockIdx.x * TP) / P.W);
   uint32_t tma_phase = 0;
   bool tma_pending = false;
-  for (int s0 = 0; s0 < S && !bail; s0 += kT) {
-    const int tc = min(kT, S - s0);
-    const int pc = ring_pos(s0, R);     // ring position of the chunk's first step
-    if (P.tma && s0 > 0) {
-      // this chunk's box, issued during the previous chunk
-      if (!mbar_wait(&tma_bar, tma_phase, P.wait_iters)) {
-        if (lane == 0) atomicOr(n_events, kTimeoutBit);
-        bail = 1;
-      }
-      tma_phase ^= 1;
-      tma_pending = false;
-      __syncthreads();
-      if (bail) break;
-#pragma unroll
-      for (int j = 0; j < kT; ++j)
-#pragma unroll
-        for (int t = 0; t < 9; ++t) {
-          const int col = p + t % 3 + 3, row = t / 3;
-          xn[j][t] = xbuf[((1 + j) * 3 + row) * kBoxW + col] - xbuf[(j * 3 + row) * kBoxW + col];
+  // Rounds: in round tau layer 0 computes chunk tau and tensor-core layer l
+  // chunk tau - l + 1, so that one MMA issue, one barrier and one pass of
+  // epilogues serve every layer.  Layer l's epilogue writes chunk tau - l + 1
+  // into layer l + 1's ring, over the slots that layer l + 1's MMAs of the same
+  // round read: the MMAs are issued last layer first and each epilogue waits
+  // for its own layer's commit, which follows every later layer's MMAs.
+  for (int tau = 0; tau < nch + L - 2; ++tau) {
+    // ---- layer 0 on CUDA cores, FP32, chunk tau: X_k = l_k - l_{k-1} (Eq. 1)
+    if (tau < nch) {
+      const int s0 = tau * kT, tc = min(kT, S - s0), pc = ring_pos(s0, R);
+      if (P.tma && tau > 0) {
+        // this chunk's box, issued during the previous round
+        if (!mbar_wait(&tma_bar, tma_phase, P.wait_iters)) {
+          if (lane == 0) atomicOr(n_events, kTimeoutBit);
+          bail = 1;
         }
-    }
-    float h[kT][kHalf];                 // block input (residual) / current activation, FP32
-    // ---- layer 0 on CUDA cores, FP32: X_k = l_k - l_{k-1} (Eq. 1)
+        tma_phase ^= 1;
+        tma_pending = false;
+        __syncthreads();
+        if (bail) break;
 #pragma unroll
-    for (int j = 0; j < kT; ++j) {
-      if (j >= tc) break;
-      const int f = P.f0 + s0 + j;
-      float acc[kHalf];
-#pragma unroll
-      for (int c = 0; c < kHalf; ++c) acc[c] = bs[c0 + c];
-      if (live) {
-        if (ks0 == 3) {
+        for (int j = 0; j < kT; ++j)
 #pragma unroll
           for (int t = 0; t < 9; ++t) {
-            const float* wt = w0 + t * CP + c0;
-#pragma unroll
-            for (int c = 0; c < kHalf; ++c) acc[c] = fmaf(wt[c], xn[j][t], acc[c]);
+            const int col = p + t % 3 + 3, row = t / 3;
+            xn[j][t] = xbuf[((1 + j) * 3 + row) * kBoxW + col] - xbuf[(j * 3 + row) * kBoxW + col];
           }
-        } else if (ks0 > 0) {
-          const int r0 = ks0 >> 1;
-          for (int dy = 0; dy < ks0; ++dy) {
-            const int yy = py + dy - r0;
-            if (yy < 0 || yy >= P.H) continue;
-            for (int dx = 0; dx < ks0; ++dx) {
-              const int xx = px + dx - r0;
-              if (xx < 0 || xx >= P.W) continue;
-              const int64_t qq = (int64_t)yy * P.W + xx;
-              const float xc = __ldg(logl + (int64_t)f * npix + qq);
-              const float xp = f == 0 ? last_l[qq] : __ldg(logl + (int64_t)(f - 1) * npix + qq);
-              const float v = xc - xp;
-              const float* wt = w0 + (dy * ks0 + dx) * CP + c0;
+      }
+      if (worker) {
+      float h0[kT][kHalf];
+#pragma unroll
+      for (int j = 0; j < kT; ++j) {
+#pragma unroll
+        for (int c = 0; c < kHalf; ++c) h0[j][c] = 0.0f;
+        if (j >= tc) continue;
+        const int f = P.f0 + s0 + j;
+        float acc[kHalf];
+#pragma unroll
+        for (int c = 0; c < kHalf; ++c) acc[c] = bs[c0 + c];
+        if (live) {
+          if (ks0 == 3) {
+#pragma unroll
+            for (int t = 0; t < 9; ++t) {
+              const float* wt = w0 + t * CP + c0;
+#pragma unroll
+              for (int c = 0; c < kHalf; ++c) acc[c] = fmaf(wt[c], xn[j][t], acc[c]);
+            }
+          } else if (ks0 > 0) {
+            const int r0 = ks0 >> 1;
+            for (int dy = 0; dy < ks0; ++dy) {
+              const int yy = py + dy - r0;
+              if (yy < 0 || yy >= P.H) continue;
+              for (int dx = 0; dx < ks0; ++dx) {
+                const int xx = px + dx - r0;
+                if (xx < 0 || xx >= P.W) continue;
+                const int64_t qq = (int64_t)yy * P.W + xx;
+                const float xc = __ldg(logl + (int64_t)f * npix + qq);
+                const float xp = f == 0 ? last_l[qq] : __ldg(logl + (int64_t)(f - 1) * npix + qq);
+                const float v = xc - xp;
+                const float* wt = w0 + (dy * ks0 + dx) * CP + c0;
+#pragma unroll
+                for (int c = 0; c < kHalf; ++c) acc[c] = fmaf(wt[c], v, acc[c]);
+              }
+            }
+          } else {
+            const float xc = __ldg(logl + (int64_t)f * npix + q);
+            const float xp = f == 0 ? last_l[q] : __ldg(logl + (int64_t)(f - 1) * npix + q);
+            xh[ring_pos(s0 + j, R) * TP + p] = xc - xp;
+            for (int tau0 = 0; tau0 < kt; ++tau0) {
+              const float v = xh[ring_pos(s0 + j - hk + tau0, R) * TP + p];
+              const float* wt = w0 + tau0 * CP + c0;
 #pragma unroll
               for (int c = 0; c < kHalf; ++c) acc[c] = fmaf(wt[c], v, acc[c]);
             }
           }
-        } else {
-          const float xc = __ldg(logl + (int64_t)f * npix + q);
-          const float xp = f == 0 ? last_l[q] : __ldg(logl + (int64_t)(f - 1) * npix + q);
-          xh[ring_pos(s0 + j, R) * TP + p] = xc - xp;
-          for (int tau = 0; tau < kt; ++tau) {
-            const float v = xh[ring_pos(s0 + j - hk + tau, R) * TP + p];
-            const float* wt = w0 + tau * CP + c0;
-#pragma unroll
-            for (int c = 0; c < kHalf; ++c) acc[c] = fmaf(wt[c], v, acc[c]);
-          }
         }
-      }
 #pragma unroll
-      for (int c = 0; c < kHalf; ++c) h[j][c] = live ? fmaxf(acc[c], 0.0f) : 0.0f;
-      const int pj = pc + j >= R ? pc + j - R : pc + j;
-      store_half(slot_of(1, pj), hc, p, h[j]);
+        for (int c = 0; c < kHalf; ++c) h0[j][c] = live ? fmaxf(acc[c], 0.0f) : 0.0f;
+        const int pj = pc + j >= R ? pc + j - R : pc + j;
+        store_half(slot_of(1, pj), hc, p, h0[j]);
+      }
+      // the block input of the first residual block, kept FP32 for its closing layer
+      if (residual && L >= 3) {
+        tmem_st8x2(hb_col(0, tau & 1), hb_col(0, tau & 1) + CP, h0[0], h0[1]);
+      }
+      if (ks0 == 3 && !P.tma) load_x9(s0 + kT);   // next chunk's inputs, consumed next round
+      }
     }
-    if (ks0 == 3 && !P.tma) load_x9(s0 + kT);   // next chunk's inputs, consumed after these layers
-    // ---- layers 1 .. L-1 on the tensor core
-    for (int l = 1; l < L; ++l) {
-      fence_proxy_async_smem();
-      tc_fence_before();
-      __syncthreads();
-      tc_fence_after();
-      if (l == 1 && P.tma && tid == 0 && s0 + kT < S) {
+    // ---- every tensor-core layer's MMAs, last layer first
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (bail) break;
+    if (tid == kIssuer) {
+      if (P.tma && tau + 1 < nch) {
         // the next chunk's stem input (this chunk's was read before the barrier
         // above, and every thread's proxy fence orders those reads first)
         mbar_arrive_expect_tx(&tma_bar, kBoxBytes);
-        tma_load_3d(xbuf, &tmap, tx0 - 4, ty0 - 1, P.f0 + s0 + kT - 1, &tma_bar);
+        tma_load_3d(xbuf, &tmap, tx0 - 4, ty0 - 1, P.f0 + (tau + 1) * kT - 1, &tma_bar);
       }
-      if (l == 1 && P.tma && s0 + kT < S) tma_pending = true;
-      if (tid == 0) {
+      constexpr uint64_t kBlock = (CP * 16) >> 4;   // one 16-row block of the strip
+      for (int l = L - 1; l >= 1; --l) {
+        const int c = tau - l + 1;
+        if (c < 0 || c >= nch) continue;
+        const int s0 = c * kT, tc = min(kT, S - s0);
         // descriptors differ only in their start-address field (16-byte units):
-        // slots are 4 KB apart, B blocks 512 B
+        // slots are 4 KB apart, B blocks 256 B
         const uint64_t a0 = a_desc0 + (uint64_t)((l - 1) * R) * (kSlot >> 4);
         const uint64_t b0 = b_desc0 + (uint64_t)((l - 1) * kt) * ((CP * CP * 2) >> 4);
-        constexpr uint64_t kBlock = (CP * 16) >> 4;   // one 16-row block of the strip
         const int p0 = ring_pos(s0 - hk, R);
         auto a_of = [&](int i) {
           const int pos = p0 + i >= R ? p0 + i - R : p0 + i;
           return a0 + (uint64_t)pos * (kSlot >> 4);
         };
+        const uint32_t d = tmem + (uint32_t)((l - 1) * kT * CP);
         // slot 0 starts step 0 (tap 0), slot kt starts step 1 (tap kt - 1);
         // slots 1 .. kt - 1 add to both (taps i and i - 1)
-        umma_bf16(tmem, a_of(0), b0 + (uint64_t)(kt - 1) * kBlock, idesc16, 0);
-        if (tc > 1) umma_bf16(tmem + CP, a_of(kt), b0, idesc16, 0);
-        for (int i = 1; i < kt; ++i) umma_bf16(tmem, a_of(i), b0 + (uint64_t)(kt - 1 - i) * kBlock, idesc32, 1);
-        umma_commit(&mma_bar);
+        umma_bf16(d, a_of(0), b0 + (uint64_t)(kt - 1) * kBlock, idesc16, 0);
+        if (tc > 1) umma_bf16(d + CP, a_of(kt), b0, idesc16, 0);
+        for (int i = 1; i < kt; ++i) umma_bf16(d, a_of(i), b0 + (uint64_t)(kt - 1 - i) * kBlock, idesc32, 1);
+        umma_commit(&lbar[l]);
       }
-      const bool ok = mbar_wait(&mma_bar, phase, P.wait_iters);
-      phase ^= 1;
-      if (!ok) {
+    }
+    if (P.tma && tau + 1 < nch) tma_pending = true;
+    // ---- epilogues, last layer first, each after its own layer's commit
+    for (int l = L - 1; l >= 1 && worker; --l) {
+      const int c = tau - l + 1;
+      if (c < 0 || c >= nch) continue;
+      const int s0 = c * kT, tc = min(kT, S - s0), pc = ring_pos(s0, R);
+      if (!mbar_wait(&lbar[l], (lphase >> l) & 1u, P.wait_iters)) {
+        // give up: the results are not used (the state is left untouched)
         if (lane == 0) atomicOr(n_events, kTimeoutBit);
         bail = 1;
       }
+      lphase ^= 1u << l;
       tc_fence_after();
-      __syncthreads();
-      if (bail) break;
-      const bool closing = P.kind == ET_NET_RESIDUAL && (l % 2) == 0;
-      const bool inner = P.kind == ET_NET_RESIDUAL && (l % 2) == 1;
-      // both steps' accumulators (the second is unused when tc == 1)
-      float accs[kT][kHalf];
-      tmem_ld8x2(tmem + lane_base + c0, tmem + lane_base + CP + c0, accs[0], accs[1]);
+      const bool closing = residual && (l % 2) == 0;
+      const bool inner = residual && (l % 2) == 1;
+      float accs[kT][kHalf], hin[kT][kHalf];
+      tmem_ld8x2(acc_col(l), acc_col(l) + CP, accs[0], accs[1]);
+      if (closing) tmem_ld8x2(hb_col(l / 2 - 1, c & 1), hb_col(l / 2 - 1, c & 1) + CP, hin[0], hin[1]);
+      float out[kT][kHalf];
 #pragma unroll
-      for (int j = 0; j < kT; ++j) {
-        if (j >= tc) break;
-        const float* acc = accs[j];
-        float out[kHalf];
+      for (int j = 0; j < kT; ++j)
 #pragma unroll
-        for (int c = 0; c < kHalf; ++c) {
-          const float v = acc[c] + bs[l * CP + c0 + c];
-          if (closing) { h[j][c] = fmaxf(h[j][c] + v, 0.0f); out[c] = h[j][c]; }
-          else if (inner) out[c] = fmaxf(v, 0.0f);
-          else { out[c] = fmaxf(v, 0.0f); h[j][c] = out[c]; }
-          if (!live) out[c] = 0.0f;
+        for (int c2 = 0; c2 < kHalf; ++c2) {
+          const float v = accs[j][c2] + bs[l * CP + c0 + c2];
+          float o = closing ? fmaxf(hin[j][c2] + v, 0.0f) : fmaxf(v, 0.0f);
+          out[j][c2] = (live && j < tc) ? o : 0.0f;
         }
-        if (l + 1 < L) {
+      (void)inner;
+      if (l + 1 < L) {
+#pragma unroll
+        for (int j = 0; j < kT; ++j) {
+          if (j >= tc) break;
           const int pj = pc + j >= R ? pc + j - R : pc + j;
-          store_half(slot_of(l + 1, pj), hc, p, out);
-        } else {
+          store_half(slot_of(l + 1, pj), hc, p, out[j]);
+        }
+        // a closing layer's output is the next block's input
+        if (closing && l + 2 < L) tmem_st8x2(hb_col(l / 2, c & 1), hb_col(l / 2, c & 1) + CP, out[0], out[1]);
+      } else {
+        // ---- Eq. 6 projection (each half its 8 channels) and BiLIF, step by step
 #pragma unroll
-          for (int c = 0; c < kHalf; ++c) h[j][c] = out[c];
+        for (int j = 0; j < kT; ++j) {
+          if (j >= tc) break;
+          float Ih = hc == 0 ? bp[0] : 0.0f;
+#pragma unroll
+          for (int c2 = 0; c2 < kHalf; ++c2) Ih = fmaf(wp[c0 + c2], out[j][c2], Ih);
+          if (hc == 1) part[j][p] = Ih;
+        }
+        workers_sync();
+        if (hc == 0) {
+#pragma unroll
+          for (int j = 0; j < kT; ++j) {
+            if (j >= tc) break;
+            const int f = P.f0 + s0 + j;
+            uint32_t nev = 0;
+            int Sp = 0;
+            if (live) {
+              float I = bp[0];
+#pragma unroll
+              for (int c2 = 0; c2 < kHalf; ++c2) I = fmaf(wp[c2], out[j][c2], I);
+              I += part[j][p];
+              const float vp = P.beta * V + I;
+              Sp = vp >= P.vth ? 1 : (vp <= -P.vth ? -1 : 0);
+              V = vp - P.reset * (float)Sp;
+              nev = (Sp != 0 && P.t0 + f >= 0) ? 1u : 0u;   // delayed labels below 0: none
+              const int64_t o = (int64_t)(s0 + j) * npix + q;
+              if (I_out) I_out[o] = I;
+              if (spikes) spikes[o] = (int8_t)Sp;
+            }
+            emit_events_warp(events, cap, n_events, nev, (uint32_t)px, (uint32_t)py, (uint32_t)(P.t0 + f), Sp);
+          }
         }
       }
-      tc_fence_before();
     }
-    if (bail) break;
-    // ---- Eq. 6 projection (each half its 8 channels) and BiLIF, step by step
-#pragma unroll
-    for (int j = 0; j < kT; ++j) {
-      if (j >= tc) break;
-      float Ih = hc == 0 ? bp[0] : 0.0f;
-#pragma unroll
-      for (int c = 0; c < kHalf; ++c) Ih = fmaf(wp[c0 + c], h[j][c], Ih);
-      if (hc == 1) part[j][p] = Ih;
-    }
-    __syncthreads();
-    if (hc == 0) {
-#pragma unroll
-      for (int j = 0; j < kT; ++j) {
-        if (j >= tc) break;
-        const int f = P.f0 + s0 + j;
-        uint32_t nev = 0;
-        int Sp = 0;
-        if (live) {
-          float I = bp[0];
-#pragma unroll
-          for (int c = 0; c < kHalf; ++c) I = fmaf(wp[c], h[j][c], I);
-          I += part[j][p];
-          const float vp = P.beta * V + I;
-          Sp = vp >= P.vth ? 1 : (vp <= -P.vth ? -1 : 0);
-          V = vp - P.reset * (float)Sp;
-          nev = (Sp != 0 && P.t0 + f >= 0) ? 1u : 0u;   // delayed labels below 0: none
-          const int64_t o = (int64_t)(s0 + j) * npix + q;
-          if (I_out) I_out[o] = I;
-          if (spikes) spikes[o] = (int8_t)Sp;
-        }
-        emit_events_warp(events, cap, n_events, nev, (uint32_t)px, (uint32_t)py, (uint32_t)(P.t0 + f), Sp);
-      }
-    }
+    tmem_wait_st();
+    tc_fence_before();
   }
   __syncthreads();
   if (bail) {
-    // a bounded wait gave up: give the MMAs and the TMA still in flight a
-    // second bounded wait
-    mbar_wait(&mma_bar, phase ^ 1u, kDrainIters);
+    // a bounded wait gave up: one more commit tracks every MMA still in
+    // flight; wait for it, and for the TMA, with a second bounded wait
+    if (tid == kIssuer) umma_commit(&drain_bar);
+    mbar_wait(&drain_bar, 0, kDrainIters);
     if (tma_pending) mbar_wait(&tma_bar, tma_phase, kDrainIters);
   } else if (live) {
     if (hc == 0) Vg[q] = V;

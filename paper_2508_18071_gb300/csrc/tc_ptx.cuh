@@ -145,3 +145,21 @@ __device__ __forceinline__ void tmem_ld8x2(uint32_t taddr0, uint32_t taddr1, flo
     v1[i] = __uint_as_float(r[8 + i]);
   }
 }
+
+// Two 32 x 32b x 8 stores (8 registers per thread into columns taddr0 .. +7
+// and taddr1 .. +7 of the thread's lane); complete after tmem_wait_st.
+__device__ __forceinline__ void tmem_st8x2(uint32_t taddr0, uint32_t taddr1, const float* v0, const float* v1) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr0),
+      "r"(__float_as_uint(v0[0])), "r"(__float_as_uint(v0[1])), "r"(__float_as_uint(v0[2])),
+      "r"(__float_as_uint(v0[3])), "r"(__float_as_uint(v0[4])), "r"(__float_as_uint(v0[5])),
+      "r"(__float_as_uint(v0[6])), "r"(__float_as_uint(v0[7]))
+      : "memory");
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr1),
+      "r"(__float_as_uint(v1[0])), "r"(__float_as_uint(v1[1])), "r"(__float_as_uint(v1[2])),
+      "r"(__float_as_uint(v1[3])), "r"(__float_as_uint(v1[4])), "r"(__float_as_uint(v1[5])),
+      "r"(__float_as_uint(v1[6])), "r"(__float_as_uint(v1[7]))
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
