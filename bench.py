@@ -501,7 +501,8 @@ def _thr(api, frames, t0, dev):
     return api.threshold_events(frames, C_THR, ref, False, t0=t0).host()
 
 
-def event_gate(api, inputs, g, net, dev, stream, s0, nb, spp, W, H, warm=64, n_1024=26, n_thr=26):
+def event_gate(api, inputs, g, net, dev, stream, s0, nb, spp, W, H, warm=64, n_1024=26, n_thr=26,
+               net_f32=None):
     """Event F1 (delta = 0, 1, 2 frames; matching per pixel and polarity) of the
     method -- EvSNet on `spp` frames, its state carried in from the `warm`
     frames before -- against 256-SPP + threshold on the nb frames from s0; next
@@ -532,11 +533,18 @@ def event_gate(api, inputs, g, net, dev, stream, s0, nb, spp, W, H, warm=64, n_1
                       first_frame=s0 - warm, logl=lw, want_rgb=False)
     st = api.EvsStateDev(net, H, W)
     api.evsnet_forward(lw, net, st, t0=s0 - warm)
+    if net_f32 is not None:
+        st32 = api.EvsStateDev(net_f32, H, W)
+        api.evsnet_forward(lw, net_f32, st32, t0=s0 - warm)
     del lw
     lm = torch.empty((nb, H, W), dtype=torch.float32, device=dev)
     api.render_frames(g, bpath, W, H, spp, DEPTH, SEED, first_frame=s0, logl=lm, want_rgb=False)
     m_ev = _win(api.evsnet_forward(lm, net, st, t0=s0)[0].host(), lo, hi)
     out["method"] = _f1s(api, m_ev, ref_ev)
+    if net_f32 is not None:
+        # the same network with FP32 convolutions (the precision it was trained in)
+        out["method_f32_convolutions"] = _f1s(
+            api, _win(api.evsnet_forward(lm, net_f32, st32, t0=s0)[0].host(), lo, hi), ref_ev)
     out["n_ref"], out["n_method"] = len(ref_ev), len(m_ev)
     fr = train_evsnet.fixed_rate_events(ref_ev, hi - lo, H, W, lo)
     out["fixed_rate_control"] = _f1s(api, fr, ref_ev)
@@ -884,8 +892,9 @@ def main():
 
     # ---- the metric's baseline: 256 spp + contrast threshold, same kernels
     if not args.no_baseline:
+        net_f32 = api.EvsNetDev.from_dict(net_d, _lib.ET_F32) if dtype != _lib.ET_F32 else None
         gate = event_gate(api, inputs, g, net, dev, stream, first + 10000, args.baseline_frames, args.spp,
-                          W_, H_)
+                          W_, H_, net_f32=net_f32)
         base_value = gate.pop("_baseline_value")
         line["baseline_256spp_threshold"] = {
             "value": base_value, "unit": UNIT, "frames_measured": args.baseline_frames,
