@@ -416,14 +416,17 @@ def run_rows(args):
     E = torch.as_tensor(np.random.default_rng(1).choice([-1, 0, 0, 0, 0, 0, 1], (B, K, S, S))
                         .astype(np.float32)).cuda()
     d3 = inputs.random_evsnet(0, 4, 16, 1, 3, seed=2, vth=0.2, beta=0.9)
+    dt7 = inputs.random_evsnet(1, 7, 16, 7, 1, seed=2, vth=0.2, beta=0.9, std=0.05)
+    dst = inputs.random_evsnet(1, 7, 16, 7, 1, seed=2, vth=0.2, beta=0.9, std=0.05, ks0=3)
     for name, d, tdt in (("training_step_3x3", d3, _lib.ET_F32),
                          ("training_step_3x3_bf16", d3, _lib.ET_BF16),
-                         ("training_step_temporal", inputs.random_evsnet(1, 7, 16, 7, 1, seed=2, vth=0.2,
-                                                                          beta=0.9, std=0.05), _lib.ET_F32)):
+                         ("training_step_temporal", dt7, _lib.ET_F32),
+                         ("training_step_temporal_bf16", dt7, _lib.ET_BF16),
+                         ("training_step_stem_temporal", dst, _lib.ET_F32),
+                         ("training_step_stem_temporal_bf16", dst, _lib.ET_BF16)):
         T = training.Trainer(d, lr=1e-3, dtype=tdt)
         t = gtime(lambda: T.step(clips, E))
-        C_, Ln, kt, ks = d["C"], d["n_layers"], d["kt"], d["ks"]
-        macs = kt * ks * ks * C_ + (Ln - 1) * kt * ks * ks * C_ * C_ + C_
+        macs = macs_per_pixel_step(d)
         # forward, its recompute in the backward, data and weight gradients
         flops = 4 * 2.0 * macs * B * K * S * S
         onet = oracle.EvsNet.from_dict(d)
@@ -436,9 +439,9 @@ def run_rows(args):
                                    "work": "4 x %d MAC per pixel-step (forward, recomputed forward, "
                                            "data and weight gradients)" % macs,
                                    "note": ("FP32 CUDA cores" if tdt == _lib.ET_F32 else
-                                            "forward and data-gradient convolutions of layers 1.. in "
-                                            "BF16 on the tensor cores, the rest FP32 on CUDA cores; "
-                                            "peak = the FP32 one, for comparison")},
+                                            "forward, data-gradient and weight-gradient convolutions "
+                                            "of layers 1.. in BF16 on the tensor cores, the rest FP32 "
+                                            "on CUDA cores; peak = the FP32 one, for comparison")},
                       "cpu_baseline": {"ms_per_step": tc * 1e3 * (B * K * S * S) / (16 * 32 * 32),
                                        "kind": "oracle (float64 torch autograd)",
                                        "cores": torch.get_num_threads(),

@@ -608,8 +608,11 @@ int check(const et_evsnet_weights* net, const et_train_shape* sh) {
   const bool spatial = net->kind == ET_NET_STACK && net->ks == 3 && net->kt == 1 && net->C <= kMaxC &&
                        net->ks0 == 0;
   if (!spatial && !et_train_is_temporal(net)) return ET_ERR_UNIMPLEMENTED;
-  // BF16: the spatial form's C -> C convolutions on the tensor cores
-  if (net->dtype != ET_F32 && !(net->dtype == ET_BF16 && spatial)) return ET_ERR_UNIMPLEMENTED;
+  // BF16: the C -> C convolutions of the spatial form, or of the temporal form
+  // (kt <= 7), on the tensor cores
+  if (net->dtype != ET_F32 &&
+      !(net->dtype == ET_BF16 && (spatial || (!spatial && et_train_tct_supported(net)))))
+    return ET_ERR_UNIMPLEMENTED;
   if (sh->ckpt_every > kMaxSeg) return ET_ERR_UNIMPLEMENTED;
   return ET_OK;
 }

@@ -32,3 +32,17 @@ int et_train_tc_conv(const float* in, int N, int C, int H, int W, const float* w
 // grad b[co] += sum dz[co][p] (FP32 accumulation; added to gw / gb).
 int et_train_tc_wgrad(const float* dz, const float* act, int N, int C, int H, int W, float* gw,
                       float* gb, cudaStream_t stream);
+
+// The temporal form's C -> C layers on the tensor cores (BF16 operands, FP32
+// accumulation; train_tct.cu), activations [B][K][hw][C] with C <= 16 and
+// kt <= 7: forward out = ReLU(conv(in) + b (+ extra)), with I = bp + wp . out
+// when I is not NULL; or, with data_grad, out = (extra + conv^T(in)) *
+// 1(mask > 0), in being dL/dz of the layer's output.
+bool et_train_tct_supported(const et_evsnet_weights* net);
+int et_train_tct_conv(const float* in, int B, int K, int64_t hw, int C, int kt, const float* w, const float* b,
+                      const float* extra, const float* mask, float* out, const float* wp, const float* bp,
+                      float* I, bool data_grad, cudaStream_t st);
+// Its weight and bias gradients: grad w[co][ci][tau] += sum dz[k][co]
+// in[k - (kt-1) + tau][ci], grad b[co] += sum dz[k][co] (added to gw / gb).
+int et_train_tct_wgrad(const float* dz, const float* in, int B, int K, int64_t hw, int C, int kt, float* gw,
+                       float* gb, cudaStream_t st);

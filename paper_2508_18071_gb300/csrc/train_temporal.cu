@@ -18,6 +18,12 @@
 #include "evsnet_common.h"
 #include "train_api.h"
 
+#define ET_TRY(expr)                 \
+  do {                               \
+    const int rc_ = (expr);          \
+    if (rc_ != ET_OK) return rc_;    \
+  } while (0)
+
 namespace {
 
 constexpr int kMaxC = 16;
@@ -649,6 +655,13 @@ int tforward(const float* logl, const et_train_shape* sh, const et_evsnet_weight
   for (int l = 1; l < L; ++l) {
     // residual form: even layers close a block and add its input
     const float* res = (net->kind == ET_NET_RESIDUAL && l % 2 == 0) ? ws.act[l - 2] : nullptr;
+    if (net->dtype == ET_BF16) {
+      const int rc = et_train_tct_conv(ws.act[l - 1], sh->B, sh->K, hw, C, kt, net->w + twofs(l, C, kt, n0),
+                                       net->b + (int64_t)l * C, res, nullptr, ws.act[l], wp, bp,
+                                       l == L - 1 ? ws.I : nullptr, false, st);
+      if (rc != ET_OK) return rc;
+      continue;
+    }
     auto kern = C == CP ? tconv16_fwd<true> : tconv16_fwd<false>;
     kern<<<grid2, 256, 0, st>>>(ws.act[l - 1], sh->B, sh->K, hw, C, kt, net->w + twofs(l, C, kt, n0),
                                net->b + (int64_t)l * C, res, ws.act[l], wp, bp,
@@ -722,23 +735,34 @@ int et_train_temporal_backward(const float* logl, const et_train_shape* sh,
   const unsigned wgrid16 = (unsigned)std::max<int64_t>(
       1, std::min<int64_t>((int64_t)nsm * std::max(wblocks, 1), (n + kPts16 - 1) / kPts16));
   auto dkern = C == CP ? tconv16_bwd_data<true> : tconv16_bwd_data<false>;
-  auto wgrad = [&](const float* d, int l) {
+  auto wgrad = [&](const float* d, int l) -> int {
     if (l == 0 && net->ks0 > 0)
       tstem_bwd_weight<<<wgrid, 256, 0, st>>>(d, logl, B, K, sh->H, sh->W, C, net->ks0, grad_w, grad_b);
     else if (l == 0)
       tconv_bwd_weight<<<wgrid, 256, 0, st>>>(d, logl, B, K, hw, C, kt, grad_w, grad_b);
+    else if (net->dtype == ET_BF16)
+      return et_train_tct_wgrad(d, ws.act[l - 1], B, K, hw, C, kt, grad_w + twofs(l, C, kt, n0),
+                                grad_b + (int64_t)l * C, st);
     else
       wkern<<<wgrid16, wthr, wsmem, st>>>(d, ws.act[l - 1], B, K, hw, C, kt, grad_w + twofs(l, C, kt, n0),
                                           grad_b + (int64_t)l * C);
+    return ET_OK;
+  };
+  // data gradient through layer l: out = (add + conv_l^T(d)) * 1(mask > 0)
+  auto dgrad = [&](const float* d, int l, const float* add, const float* mask, float* out) -> int {
+    if (net->dtype == ET_BF16)
+      return et_train_tct_conv(d, B, K, hw, C, kt, net->w + twofs(l, C, kt, n0), nullptr, add, mask, out,
+                               nullptr, nullptr, nullptr, true, st);
+    dkern<<<grid2, 256, 0, st>>>(d, B, K, hw, C, kt, net->w + twofs(l, C, kt, n0), add, mask, out);
+    return ET_OK;
   };
   if (net->kind == ET_NET_STACK) {
     int cur = 0;
     for (int l = L - 1; l >= 0; --l) {
-      wgrad(ws.g[cur], l);
+      ET_TRY(wgrad(ws.g[cur], l));
       ET_CHECK_LAUNCH();
       if (l > 0) {
-        dkern<<<grid2, 256, 0, st>>>(ws.g[cur], B, K, hw, C, kt, net->w + twofs(l, C, kt, n0), nullptr,
-                                    ws.act[l - 1], ws.g[cur ^ 1]);
+        ET_TRY(dgrad(ws.g[cur], l, nullptr, ws.act[l - 1], ws.g[cur ^ 1]));
         ET_CHECK_LAUNCH();
         cur ^= 1;
       }
@@ -750,21 +774,19 @@ int et_train_temporal_backward(const float* logl, const et_train_shape* sh,
   for (int i = (L - 1) / 2; i >= 1; --i) {
     const int la = 2 * i - 1, lc = 2 * i;
     const int cy = (cz + 1) % 3, cn = (cz + 2) % 3;
-    wgrad(ws.g[cz], lc);
+    ET_TRY(wgrad(ws.g[cz], lc));
     ET_CHECK_LAUNCH();
     // dy = conv_lc^T(dz) masked by a > 0
-    dkern<<<grid2, 256, 0, st>>>(ws.g[cz], B, K, hw, C, kt, net->w + twofs(lc, C, kt, n0), nullptr,
-                                ws.act[la], ws.g[cy]);
+    ET_TRY(dgrad(ws.g[cz], lc, nullptr, ws.act[la], ws.g[cy]));
     ET_CHECK_LAUNCH();
-    wgrad(ws.g[cy], la);
+    ET_TRY(wgrad(ws.g[cy], la));
     ET_CHECK_LAUNCH();
     // dz_prev = (dz + conv_la^T(dy)) masked by h_{i-1} > 0
-    dkern<<<grid2, 256, 0, st>>>(ws.g[cy], B, K, hw, C, kt, net->w + twofs(la, C, kt, n0), ws.g[cz],
-                                ws.act[la - 1], ws.g[cn]);
+    ET_TRY(dgrad(ws.g[cy], la, ws.g[cz], ws.act[la - 1], ws.g[cn]));
     ET_CHECK_LAUNCH();
     cz = cn;
   }
-  wgrad(ws.g[cz], 0);
+  ET_TRY(wgrad(ws.g[cz], 0));
   ET_CHECK_LAUNCH();
   return ET_OK;
 }

@@ -143,13 +143,3 @@ def test_bf16_training_wait_timeout_leaves_nan_and_recovers(tr):
         lib.et_set_wait_budget(-1)
     again = tr.train_forward(lf, meta, meta.w, meta.b, ckpt_every=8, want_I=True)["I"]
     assert torch.equal(again, ref)
-
-
-def test_bf16_training_rejects_the_temporal_form(tr):
-    from paper_2508_18071_gb300 import _lib, api
-    d = inputs.random_evsnet(1, 3, 8, 7, 1, seed=3)
-    meta = api.EvsNetDev.from_dict(d, _lib.ET_BF16)
-    lf = torch.zeros((1, 5, 8, 8), device="cuda")
-    with pytest.raises(_lib.ETError) as e:
-        tr.train_forward(lf, meta, meta.w, meta.b, ckpt_every=4)
-    assert e.value.status == _lib.ET_ERR_UNIMPLEMENTED
