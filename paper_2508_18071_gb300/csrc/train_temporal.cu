@@ -227,16 +227,16 @@ tproj_bwd(const float* __restrict__ dI, const float* __restrict__ h, int64_t n, 
 
 // ------------------------------------------------- weight backward, layer 0
 // grad w[co][tau] += sum dz[k][co] X[k - kt + 1 + tau]; grad b[co] += sum dz[k][co].
-// Persistent blocks stage 32 pixel-steps at a time in shared memory; each
-// thread owns a few (co, tau) entries, one atomic per entry per block.
-constexpr int kPts = 32;
+// Persistent blocks stage 128 pixel-steps at a time in shared memory; each
+// thread owns a (co, tau) entry, one atomic per entry per block.
+constexpr int kPts = 128;
 __global__ void __launch_bounds__(256)
 tconv_bwd_weight(const float* __restrict__ dz, const float* __restrict__ logl, int B, int K,
                  int64_t hw, int C, int kt, float* __restrict__ gw, float* __restrict__ gb) {
   constexpr int Cin = 1;
   __shared__ float sd[kPts][kMaxC];
-  __shared__ float sx[kPts][kMaxC * kMaxKt + 1];   // [ci][tau], padded
-  constexpr int kPer = (kMaxC * kMaxC * kMaxKt + kMaxC + 255) / 256;
+  __shared__ float sx[kPts][kMaxKt + 1];   // [tau], padded
+  constexpr int kPer = (kMaxC * kMaxKt + kMaxC + 255) / 256;
   float acc[kPer];
 #pragma unroll
   for (int j = 0; j < kPer; ++j) acc[j] = 0.0f;
