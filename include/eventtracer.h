@@ -133,13 +133,15 @@ int et_scene_info(const et_scene* scene, int64_t* n_tris, int64_t* n_nodes, doub
  *   cams      host [n_frames] cameras (copied; the pointer may be reused at once)
  *   rgb       device float [n_frames][H][W][3] mean linear radiance, or NULL
  *   logl      device float [n_frames][H][W] Eq. 1 log luminance, or NULL:
- *             log_mode ET_LOG_EPS: ln(L + log_param); ET_LOG_PAPER: rho = log_param
+ *             log_mode ET_LOG_EPS: ln(L + log_param); ET_LOG_PAPER: rho = log_param;
+ *             evaluated in FP32 (within 1 ulp of the correctly rounded value)
  *   records   device int32 [n_frames][H][W][spp][max_depth][2] or NULL: per path
  *             segment the triangle hit (-1 miss, -2 not traced) and the light
  *             sampling record (2 * light + visible, -1 none) -- for testing
  * Calls on one scene must be issued on one stream (the scene holds the cameras).
  * Errors: ET_ERR_ARG (W, H, spp, max_depth out of [1, 65535] / [1, 4096] / [1, 16],
- * n_frames < 0, both outputs NULL), ET_ERR_CUDA. */
+ * n_frames < 0, both outputs NULL), ET_ERR_UNIMPLEMENTED (the wavefront
+ * schedules with W x H >= 2^31 pixels), ET_ERR_CUDA. */
 int et_render_frames(const et_scene* scene, const et_camera* cams, int32_t n_frames,
                      int32_t first_frame, int32_t W, int32_t H, int32_t spp,
                      int32_t max_depth, uint64_t seed, float* rgb, float* logl,

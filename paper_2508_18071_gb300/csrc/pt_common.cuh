@@ -396,13 +396,13 @@ __device__ __forceinline__ bool continue_path(const Vertex& v, uint32_t pix, uin
   return true;
 }
 
-// Eq. 1 log map of the pixel's mean radiance (luminance in FP32, log in FP64).
+// Eq. 1 log map of the pixel's mean radiance, luminance and log in FP32 (logf:
+// at most 1 ulp from the correctly rounded logarithm); the oracle evaluates the
+// log in FP64.
 __device__ __forceinline__ float log_luminance(f3 m, int log_mode, float log_param) {
   const float Lum = 0.2126f * m.x + 0.7152f * m.y + 0.0722f * m.z;
-  double l;
-  if (log_mode == ET_LOG_EPS) l = log((double)Lum + (double)log_param);
-  else l = (Lum >= log_param) ? log((double)Lum) : (log((double)log_param) / (double)log_param) * (double)Lum;
-  return (float)l;
+  if (log_mode == ET_LOG_EPS) return logf(Lum + log_param);
+  return Lum >= log_param ? logf(Lum) : (logf(log_param) / log_param) * Lum;
 }
 
 }  // namespace pt

@@ -16,6 +16,7 @@
 // (the same order as the one-kernel schedule) and writes RGB and Eq. 1 log
 // luminance.  Queues are compacted with one atomic per warp.
 #include <algorithm>
+#include <cub/block/block_radix_sort.cuh>
 #include <cub/device/device_radix_sort.cuh>
 #include "et_internal.cuh"
 #include "pt_common.cuh"
@@ -48,11 +49,13 @@ struct Batch {
 };
 
 // pixel of slot i of a frame's sample plane: raster order, or 8 x 4 tiles in
-// raster order of tiles (a warp's 32 primary rays then cover a compact tile)
-__host__ __device__ __forceinline__ int64_t slot_pixel(const Batch& bt, int64_t i) {
+// raster order of tiles (a warp's 32 primary rays then cover a compact tile).
+// Index arithmetic is 32-bit: the host keeps a batch below 2^31 paths.
+__host__ __device__ __forceinline__ uint32_t slot_pixel(const Batch& bt, uint32_t i) {
   if (!bt.tiled) return i;
-  const int64_t tile = i >> 5, tx = tile % (bt.W >> 3), ty = tile / (bt.W >> 3);
-  return (ty * 4 + ((i >> 3) & 3)) * bt.W + tx * 8 + (i & 7);
+  const uint32_t tw = (uint32_t)bt.W >> 3, tile = i >> 5;
+  const uint32_t ty = tile / tw, tx = tile - ty * tw;
+  return (ty * 4 + ((i >> 3) & 3)) * (uint32_t)bt.W + tx * 8 + (i & 7);
 }
 
 // Extension rays reordered between bounces (ET_RENDER_WAVEFRONT_SORTED): the
@@ -122,11 +125,13 @@ struct Args {
 };
 
 // path q of the batch -> (frame of the call, sample, pixel)
-__device__ __forceinline__ void path_ids(const Batch& bt, int64_t q, int& f, int& s, int64_t& pix) {
-  pix = slot_pixel(bt, q % bt.npix);
-  const int64_t plane = q / bt.npix;
-  s = bt.s0 + (int)(plane % bt.ns);
-  f = bt.f0 + (int)(plane / bt.ns);
+__device__ __forceinline__ void path_ids(const Batch& bt, uint32_t q, int& f, int& s, int64_t& pix) {
+  const uint32_t npix = (uint32_t)bt.npix, ns = (uint32_t)bt.ns;
+  const uint32_t plane = q / npix;
+  pix = slot_pixel(bt, q - plane * npix);
+  const uint32_t fo = plane / ns;
+  s = bt.s0 + (int)(plane - fo * ns);
+  f = bt.f0 + (int)fo;
 }
 
 __device__ __forceinline__ int32_t* rec_of(const Args& A, int f, int s, int64_t pix) {
@@ -152,8 +157,9 @@ __global__ void __launch_bounds__(256) wf_raygen(Args A) {
   if (q >= A.bt.paths) return;
   int f, s;
   int64_t pix;
-  path_ids(A.bt, q, f, s, pix);
-  const int x = (int)(pix % A.W), y = (int)(pix / A.W) + A.y0;
+  path_ids(A.bt, (uint32_t)q, f, s, pix);
+  const uint32_t py = (uint32_t)pix / (uint32_t)A.W;
+  const int x = (int)((uint32_t)pix - py * (uint32_t)A.W), y = (int)py + A.y0;
   const pt::Cam cam = pt::load_cam(A.cams[f]);
   f3 o, d;
   pt::camera_ray(cam, A.W, A.H, x, y, (uint32_t)s, A.first_frame + (uint32_t)f, A.k0, A.k1, o, d);
@@ -317,8 +323,9 @@ wf_accumulate(Args A, float4* acc, bool first_slice, bool last_slice, float* rgb
               int log_mode, float log_param) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (int64_t)A.bt.nf * A.bt.npix) return;
-  const int fb = (int)(i / A.bt.npix);
-  const int64_t slot = i % A.bt.npix;
+  const uint32_t npix = (uint32_t)A.bt.npix;
+  const int fb = (int)((uint32_t)i / npix);
+  const int64_t slot = (uint32_t)i - (uint32_t)fb * npix;
   f3 a = mk(0.0f, 0.0f, 0.0f);
   if (!first_slice) { const float4 t = acc[i]; a = mk(t.x, t.y, t.z); }
   for (int sb = 0; sb < A.bt.ns; ++sb) {
@@ -327,7 +334,7 @@ wf_accumulate(Args A, float4* acc, bool first_slice, bool last_slice, float* rgb
   }
   if (!last_slice) { acc[i] = make_float4(a.x, a.y, a.z, 0.0f); return; }
   const f3 m = a * (1.0f / (float)A.spp);
-  const int64_t o = (int64_t)(A.bt.f0 + fb) * A.bt.npix + slot_pixel(A.bt, slot);
+  const int64_t o = (int64_t)(A.bt.f0 + fb) * A.bt.npix + slot_pixel(A.bt, (uint32_t)slot);
   if (rgb) { rgb[3 * o] = m.x; rgb[3 * o + 1] = m.y; rgb[3 * o + 2] = m.z; }
   if (logl) logl[o] = pt::log_luminance(m, log_mode, log_param);
 }
@@ -343,6 +350,32 @@ int ensure_workspace(et_scene* s, int64_t paths, int64_t acc_pix) {
   s->wf_cap = cap;
   s->wf_acc_cap = acap;
   return ET_OK;
+}
+
+// Local variant of the sort: each block of 4096 queue entries is sorted by key
+// on its own (stable, in shared memory), so that a warp's rays share direction
+// and origin cells within a window of the queue -- whose order already
+// follows the image's tiles -- at the cost of one pass over the keys.
+#ifndef ET_LOCAL_SORT
+#define ET_LOCAL_SORT 0
+#endif
+constexpr int kLsThreads = 256, kLsItems = 16, kLsTile = kLsThreads * kLsItems;
+__global__ void __launch_bounds__(kLsThreads) wf_local_sort(const uint32_t* __restrict__ key,
+                                                            uint32_t* __restrict__ perm, int64_t n_total) {
+  using BlockSort = cub::BlockRadixSort<uint32_t, kLsThreads, kLsItems, uint32_t>;
+  __shared__ typename BlockSort::TempStorage tmp;
+  const int64_t base = (int64_t)blockIdx.x * kLsTile + (int64_t)threadIdx.x * kLsItems;
+  uint32_t k[kLsItems], v[kLsItems];
+#pragma unroll
+  for (int j = 0; j < kLsItems; ++j) {
+    const int64_t i = base + j;
+    k[j] = i < n_total ? key[i] : 0xFFFFFFFFu;
+    v[j] = (uint32_t)i;
+  }
+  BlockSort(tmp).Sort(k, v, 0, kSortBits);
+#pragma unroll
+  for (int j = 0; j < kLsItems; ++j)
+    if (base + j < n_total) perm[base + j] = v[j];
 }
 
 // keys, key copies, indices and the permutation (4 x 4 B per path) plus the
@@ -379,6 +412,7 @@ int et_render_wavefront(et_scene* s, int n_frames, int first_frame, int W, int H
                         int spp, int max_depth, uint64_t seed, float* rgb, float* logl, int log_mode,
                         float log_param, int32_t* records, cudaStream_t stream) {
   const int64_t npix = (int64_t)W * (y1 - y0);
+  if (npix >= ((int64_t)1 << 31)) return ET_ERR_UNIMPLEMENTED;   // 32-bit path indices
   const int64_t planes = std::max<int64_t>(1, kPathCap / npix);
   Batch proto{};
   proto.npix = npix;
@@ -473,8 +507,14 @@ int et_render_wavefront(et_scene* s, int n_frames, int first_frame, int W, int H
           // the continuation queue's live entries hold keys below or equal to
           // the all-ones filler of the rest, and the sort is stable: the
           // first n entries of the permutation are the queue's n rays
-          ET_CHECK_CUDA(cub::DeviceRadixSort::SortPairs(stmp, stmp_bytes, skey, skey_alt, sval, sperm,
-                                                        (int)bt.paths, 0, kSortBits, stream));
+          if (ET_LOCAL_SORT) {
+            wf_local_sort<<<(unsigned)((bt.paths + kLsTile - 1) / kLsTile), kLsThreads, 0, stream>>>(
+                skey, sperm, bt.paths);
+            ET_CHECK_LAUNCH();
+          } else {
+            ET_CHECK_CUDA(cub::DeviceRadixSort::SortPairs(stmp, stmp_bytes, skey, skey_alt, sval, sperm,
+                                                          (int)bt.paths, 0, kSortBits, stream));
+          }
         }
         ET_TRY(prof_end(s, kProfShade, pe, 0, A.ctr + C_NRAY0 + cur, stream));
         if (s->dev.n_lights > 0 && b < max_depth) {
