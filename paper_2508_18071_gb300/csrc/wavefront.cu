@@ -16,7 +16,6 @@
 // (the same order as the one-kernel schedule) and writes RGB and Eq. 1 log
 // luminance.  Queues are compacted with one atomic per warp.
 #include <algorithm>
-#include <cub/block/block_radix_sort.cuh>
 #include <cub/device/device_radix_sort.cuh>
 #include "et_internal.cuh"
 #include "pt_common.cuh"
@@ -352,32 +351,6 @@ int ensure_workspace(et_scene* s, int64_t paths, int64_t acc_pix) {
   return ET_OK;
 }
 
-// Local variant of the sort: each block of 4096 queue entries is sorted by key
-// on its own (stable, in shared memory), so that a warp's rays share direction
-// and origin cells within a window of the queue -- whose order already
-// follows the image's tiles -- at the cost of one pass over the keys.
-#ifndef ET_LOCAL_SORT
-#define ET_LOCAL_SORT 0
-#endif
-constexpr int kLsThreads = 256, kLsItems = 16, kLsTile = kLsThreads * kLsItems;
-__global__ void __launch_bounds__(kLsThreads) wf_local_sort(const uint32_t* __restrict__ key,
-                                                            uint32_t* __restrict__ perm, int64_t n_total) {
-  using BlockSort = cub::BlockRadixSort<uint32_t, kLsThreads, kLsItems, uint32_t>;
-  __shared__ typename BlockSort::TempStorage tmp;
-  const int64_t base = (int64_t)blockIdx.x * kLsTile + (int64_t)threadIdx.x * kLsItems;
-  uint32_t k[kLsItems], v[kLsItems];
-#pragma unroll
-  for (int j = 0; j < kLsItems; ++j) {
-    const int64_t i = base + j;
-    k[j] = i < n_total ? key[i] : 0xFFFFFFFFu;
-    v[j] = (uint32_t)i;
-  }
-  BlockSort(tmp).Sort(k, v, 0, kSortBits);
-#pragma unroll
-  for (int j = 0; j < kLsItems; ++j)
-    if (base + j < n_total) perm[base + j] = v[j];
-}
-
 // keys, key copies, indices and the permutation (4 x 4 B per path) plus the
 // radix sort's scratch, grown on demand
 int ensure_sort_workspace(et_scene* s, int64_t paths, uint32_t** key, uint32_t** key_alt, uint32_t** val,
@@ -507,14 +480,8 @@ int et_render_wavefront(et_scene* s, int n_frames, int first_frame, int W, int H
           // the continuation queue's live entries hold keys below or equal to
           // the all-ones filler of the rest, and the sort is stable: the
           // first n entries of the permutation are the queue's n rays
-          if (ET_LOCAL_SORT) {
-            wf_local_sort<<<(unsigned)((bt.paths + kLsTile - 1) / kLsTile), kLsThreads, 0, stream>>>(
-                skey, sperm, bt.paths);
-            ET_CHECK_LAUNCH();
-          } else {
-            ET_CHECK_CUDA(cub::DeviceRadixSort::SortPairs(stmp, stmp_bytes, skey, skey_alt, sval, sperm,
-                                                          (int)bt.paths, 0, kSortBits, stream));
-          }
+          ET_CHECK_CUDA(cub::DeviceRadixSort::SortPairs(stmp, stmp_bytes, skey, skey_alt, sval, sperm,
+                                                        (int)bt.paths, 0, kSortBits, stream));
         }
         ET_TRY(prof_end(s, kProfShade, pe, 0, A.ctr + C_NRAY0 + cur, stream));
         if (s->dev.n_lights > 0 && b < max_depth) {
