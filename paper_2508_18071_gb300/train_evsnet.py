@@ -267,7 +267,7 @@ def _emd(pred, ref, lo, hi, H, W):
 
 
 def evaluate(net: dict, scene_kind="city", seeds=(900, 901, 902), n_frames=129, size=128, spp_in=2,
-             spp_ref=256, C_thr=0.2, edge=20, ceiling=True):
+             spp_ref=256, C_thr=0.2, edge=20, ceiling=True, dtype=L.ET_F32):
     """Held-out clips: event F1 at delta = 0, 1, 2 frames and the EMD of the
     trained EvSNet on low-SPP input against the threshold events of 256-SPP
     renders, next to the method without EvSNet (threshold on the same low-SPP
@@ -276,7 +276,8 @@ def evaluate(net: dict, scene_kind="city", seeds=(900, 901, 902), n_frames=129, 
     another clip's frames.  Scored on the steps away from the clip's ends
     (`edge` steps dropped at each end, where a delayed network's window is
     incomplete).  With `ceiling`, also a second independently seeded 256-SPP
-    render and a 1024-SPP render against the reference (the noise ceiling)."""
+    render and a 1024-SPP render against the reference (the noise ceiling).
+    `dtype`: the precision of the network's convolutions at inference."""
     scene = api.Scene(scene_dict(scene_kind))
     clips = []
     for s in seeds:
@@ -289,7 +290,7 @@ def evaluate(net: dict, scene_kind="city", seeds=(900, 901, 902), n_frames=129, 
             r[tag] = api.render_frames(scene, cams, size, size, spp, 5, sd, first_frame=f0,
                                        want_rgb=False)[1]
         clips.append(r)
-    gnet = api.EvsNetDev.from_dict(net)
+    gnet = api.EvsNetDev.from_dict(net, dtype)
 
     def thr(frames, f0):
         ref = torch.zeros(size * size, dtype=torch.float64, device="cuda")
@@ -344,7 +345,8 @@ def main():
     p.add_argument("--boxes", type=int, default=1, help="7-step box filters in the initial network")
     p.add_argument("--eval-frames", type=int, default=129)
     p.add_argument("--conv-dtype", default="f32", choices=["f32", "bf16"],
-                   help="training convolutions: FP32, or BF16 on the tensor cores (3x3 form)")
+                   help="training convolutions: FP32, or BF16 on the tensor cores (3x3 form, and "
+                        "temporal form with kernels up to 7)")
     p.add_argument("--out", default=os.path.join(HERE, "weights", "evsnet_city.npz"))
     a = p.parse_args()
     T, hist = train(a.scene, a.clips, a.frames, a.size, a.spp_in, a.spp_ref, (a.c_min, a.c_max),
