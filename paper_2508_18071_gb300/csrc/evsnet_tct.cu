@@ -357,25 +357,36 @@ evsnet_tct_kernel(const __grid_constant__ CUtensorMap tmap, TctParams P, const f
         tma_load_3d(xbuf, &tmap, tx0 - 4, ty0 - 1, P.f0 + (tau + 1) * kT - 1, &tma_bar);
       }
       constexpr uint64_t kBlock = (CP * 16) >> 4;   // one 16-row block of the strip
-      for (int l = L - 1; l >= 1; --l) {
+      constexpr uint64_t kSlotU = kSlot >> 4;
+      // layer l's chunk this round starts at step 2 (tau - l + 1); its first
+      // slot (step s0 - (kt - 1)) sits at ring position p0, kept without
+      // division as the layers go down (each layer one chunk later)
+      int p0 = ring_pos((tau - (L - 1) + 1) * kT - hk, R);
+      for (int l = L - 1; l >= 1; --l, p0 = p0 + kT >= R ? p0 + kT - R : p0 + kT) {
         const int c = tau - l + 1;
         if (c < 0 || c >= nch) continue;
-        const int s0 = c * kT, tc = min(kT, S - s0);
+        const int tc = min(kT, S - c * kT);
         // descriptors differ only in their start-address field (16-byte units):
         // slots are 4 KB apart, B blocks 256 B
-        const uint64_t a0 = a_desc0 + (uint64_t)((l - 1) * R) * (kSlot >> 4);
+        const uint64_t a0 = a_desc0 + (uint64_t)((l - 1) * R) * kSlotU;
         const uint64_t b0 = b_desc0 + (uint64_t)((l - 1) * kt) * ((CP * CP * 2) >> 4);
-        const int p0 = ring_pos(s0 - hk, R);
-        auto a_of = [&](int i) {
-          const int pos = p0 + i >= R ? p0 + i - R : p0 + i;
-          return a0 + (uint64_t)pos * (kSlot >> 4);
-        };
         const uint32_t d = tmem + (uint32_t)((l - 1) * kT * CP);
         // slot 0 starts step 0 (tap 0), slot kt starts step 1 (tap kt - 1);
         // slots 1 .. kt - 1 add to both (taps i and i - 1)
-        umma_bf16(d, a_of(0), b0 + (uint64_t)(kt - 1) * kBlock, idesc16, 0);
-        if (tc > 1) umma_bf16(d + CP, a_of(kt), b0, idesc16, 0);
-        for (int i = 1; i < kt; ++i) umma_bf16(d, a_of(i), b0 + (uint64_t)(kt - 1 - i) * kBlock, idesc32, 1);
+        uint64_t bw = b0 + (uint64_t)(kt - 1) * kBlock;
+        umma_bf16(d, a0 + (uint64_t)p0 * kSlotU, bw, idesc16, 0);
+        if (tc > 1) {
+          const int pl = p0 + kt >= R ? p0 + kt - R : p0 + kt;
+          umma_bf16(d + CP, a0 + (uint64_t)pl * kSlotU, b0, idesc16, 0);
+        }
+        int pos = p0;
+#pragma unroll
+        for (int i = 1; i < kMaxKt; ++i) {
+          if (i >= kt) break;
+          pos = pos + 1 == R ? 0 : pos + 1;
+          bw -= kBlock;
+          umma_bf16(d, a0 + (uint64_t)pos * kSlotU, bw, idesc32, 1);
+        }
         umma_commit(&lbar[l]);
       }
     }
