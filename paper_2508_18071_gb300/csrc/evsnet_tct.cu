@@ -42,9 +42,12 @@
 // then one row segment), each chunk's log frames f - 1 .. f + 1, rows y - 1 ..
 // y + 1 and columns x0 - 4 .. x0 + 131 arrive as one TMA box
 // (cp.async.bulk.tensor.3d; the tensor map covers the caller's log frames,
-// zero-filled outside the image, which is the stem's zero padding), issued one
-// chunk ahead by one thread and waited on through an mbarrier; the first chunk
-// of a call, whose previous frame may be the state's, is loaded by the threads.
+// zero-filled outside the image, which is the stem's zero padding), issued two
+// chunks ahead by the issuing thread into one of two buffers and waited on
+// through that buffer's mbarrier; the first chunk of a call, whose previous
+// frame may be the state's, is loaded by the threads.  Layer 0 of chunk
+// tau + 1 is computed in registers while round tau's MMAs run and stored into
+// layer 1's ring after the round's last epilogue.
 //
 // MMA waits are bounded; on expiry the kernel sets bit 62 of the event count,
 // leaves the membrane and history state untouched, waits (bounded) for its
@@ -94,6 +97,8 @@ struct TctParams {
 constexpr int kBoxW = TP + 8;
 constexpr int kBoxFloats = kBoxW * 3 * 3;
 constexpr uint32_t kBoxBytes = kBoxFloats * 4;
+// the two box buffers start 128-byte aligned (a TMA destination's alignment)
+constexpr int kBoxStride = (kBoxFloats + 31) / 32 * 32;
 
 __device__ __forceinline__ int ring_pos(int s, int R) { return ((s % R) + R) % R; }
 
@@ -138,7 +143,7 @@ evsnet_tct_kernel(const __grid_constant__ CUtensorMap tmap, TctParams P, const f
                   int8_t* __restrict__ spikes) {
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ uint64_t lbar[kMaxLayers];  // commit of tensor-core layer l's MMAs in a round
-  __shared__ uint64_t tma_bar;
+  __shared__ uint64_t tma_bar[2];       // the two TMA box buffers
   __shared__ uint64_t drain_bar;
   __shared__ uint32_t tmem_slot;
   __shared__ int bail;
@@ -162,7 +167,7 @@ evsnet_tct_kernel(const __grid_constant__ CUtensorMap tmap, TctParams P, const f
   float* w0 = bp + 4;                                          // [taps][CP] layer 0
   const int taps0 = ks0 > 0 ? ks0 * ks0 : kt;
   float* xh = w0 + taps0 * CP;                                 // [R][TP] layer-0 X ring (temporal layer 0)
-  float* xbuf = reinterpret_cast<float*>(sm + P.off_xbuf);     // [3 frames][3 rows][kBoxW] (TMA)
+  float* xbuf = reinterpret_cast<float*>(sm + P.off_xbuf);     // [2][3 frames][3 rows][kBoxW] (TMA)
   auto slot_of = [&](int l, int pos) { return rings + ((size_t)(l - 1) * R + pos) * kSlot; };
   // history element (layer l, oldest-first slot j, channel c) of this pixel in the state
   auto hidx = [&](int l, int j, int c) -> int64_t { return (((int64_t)l * hk + j) * C + c) * npix + q; };
@@ -210,7 +215,8 @@ evsnet_tct_kernel(const __grid_constant__ CUtensorMap tmap, TctParams P, const f
   if (warp == 0) tmem_alloc(&tmem_slot, kTmemCols);
   if (tid == 0) {
     for (int l = 0; l < kMaxLayers; ++l) mbar_init(&lbar[l], 1);
-    mbar_init(&tma_bar, 1);
+    mbar_init(&tma_bar[0], 1);
+    mbar_init(&tma_bar[1], 1);
     mbar_init(&drain_bar, 1);
     bail = 0;
   }
@@ -251,98 +257,117 @@ evsnet_tct_kernel(const __grid_constant__ CUtensorMap tmap, TctParams P, const f
   };
   if (ks0 == 3) load_x9(0);
   // TMA of the stem's input: the tile's row segment (tiles are whole row
-  // segments when it is used), one box per chunk
+  // segments when it is used), one box per chunk, two buffers
   const int tx0 = (int)(((int64_t)blockIdx.x * TP) % P.W), ty0 = (int)(((int64_t)blockIdx.x * TP) / P.W);
-  uint32_t tma_phase = 0;
-  bool tma_pending = false;
-  // Rounds: in round tau layer 0 computes chunk tau and tensor-core layer l
-  // chunk tau - l + 1, so that one MMA issue, one barrier and one pass of
-  // epilogues serve every layer.  Layer l's epilogue writes chunk tau - l + 1
-  // into layer l + 1's ring, over the slots that layer l + 1's MMAs of the same
-  // round read: the MMAs are issued last layer first and each epilogue waits
-  // for its own layer's commit, which follows every later layer's MMAs.
-  for (int tau = 0; tau < nch + L - 2; ++tau) {
-    // ---- layer 0 on CUDA cores, FP32, chunk tau: X_k = l_k - l_{k-1} (Eq. 1)
-    if (tau < nch) {
-      const int s0 = tau * kT, tc = min(kT, S - s0), pc = ring_pos(s0, R);
-      if (P.tma && tau > 0) {
-        // this chunk's box, issued during the previous round
-        if (!mbar_wait(&tma_bar, tma_phase, P.wait_iters)) {
-          if (lane == 0) atomicOr(n_events, kTimeoutBit);
-          bail = 1;
-        }
-        tma_phase ^= 1;
-        tma_pending = false;
-        __syncthreads();
-        if (bail) break;
+  uint32_t tma_phase[2] = {0u, 0u};     // workers: parity of the next completion per buffer
+  int tma_issued[2] = {0, 0};           // issuing thread: boxes issued per buffer
+  auto issue_box = [&](int ch) {
+    const int b = ch & 1;
+    mbar_arrive_expect_tx(&tma_bar[b], kBoxBytes);
+    tma_load_3d(xbuf + b * kBoxStride, &tmap, tx0 - 4, ty0 - 1, P.f0 + ch * kT - 1, &tma_bar[b]);
+    ++tma_issued[b];
+  };
+  // layer 0 on CUDA cores, FP32, of chunk ch into h0n: X_k = l_k - l_{k-1}
+  // (Eq. 1); the 3 x 3 stem reads its neighbours' X from xn (thread loads)
+  // or from the chunk's TMA box
+  float h0n[kT][kHalf];
+  auto stem = [&](int ch) {
+    const int s0 = ch * kT, tc = min(kT, S - s0);
+    if (P.tma && ch > 0) {
+      const int b = ch & 1;
+      if (!mbar_wait(&tma_bar[b], tma_phase[b], P.wait_iters)) {
+        if (lane == 0) atomicOr(n_events, kTimeoutBit);
+        bail = 1;
+      }
+      tma_phase[b] ^= 1u;
+      const float* xb = xbuf + b * kBoxStride;
 #pragma unroll
-        for (int j = 0; j < kT; ++j)
+      for (int j = 0; j < kT; ++j)
+#pragma unroll
+        for (int t = 0; t < 9; ++t) {
+          const int col = p + t % 3 + 3, row = t / 3;
+          xn[j][t] = xb[((1 + j) * 3 + row) * kBoxW + col] - xb[(j * 3 + row) * kBoxW + col];
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < kT; ++j) {
+#pragma unroll
+      for (int c = 0; c < kHalf; ++c) h0n[j][c] = 0.0f;
+      if (j >= tc) continue;
+      const int f = P.f0 + s0 + j;
+      float acc[kHalf];
+#pragma unroll
+      for (int c = 0; c < kHalf; ++c) acc[c] = bs[c0 + c];
+      if (live) {
+        if (ks0 == 3) {
 #pragma unroll
           for (int t = 0; t < 9; ++t) {
-            const int col = p + t % 3 + 3, row = t / 3;
-            xn[j][t] = xbuf[((1 + j) * 3 + row) * kBoxW + col] - xbuf[(j * 3 + row) * kBoxW + col];
+            const float* wt = w0 + t * CP + c0;
+#pragma unroll
+            for (int c = 0; c < kHalf; ++c) acc[c] = fmaf(wt[c], xn[j][t], acc[c]);
           }
-      }
-      if (worker) {
-      float h0[kT][kHalf];
-#pragma unroll
-      for (int j = 0; j < kT; ++j) {
-#pragma unroll
-        for (int c = 0; c < kHalf; ++c) h0[j][c] = 0.0f;
-        if (j >= tc) continue;
-        const int f = P.f0 + s0 + j;
-        float acc[kHalf];
-#pragma unroll
-        for (int c = 0; c < kHalf; ++c) acc[c] = bs[c0 + c];
-        if (live) {
-          if (ks0 == 3) {
-#pragma unroll
-            for (int t = 0; t < 9; ++t) {
-              const float* wt = w0 + t * CP + c0;
-#pragma unroll
-              for (int c = 0; c < kHalf; ++c) acc[c] = fmaf(wt[c], xn[j][t], acc[c]);
-            }
-          } else if (ks0 > 0) {
-            const int r0 = ks0 >> 1;
-            for (int dy = 0; dy < ks0; ++dy) {
-              const int yy = py + dy - r0;
-              if (yy < 0 || yy >= P.H) continue;
-              for (int dx = 0; dx < ks0; ++dx) {
-                const int xx = px + dx - r0;
-                if (xx < 0 || xx >= P.W) continue;
-                const int64_t qq = (int64_t)yy * P.W + xx;
-                const float xc = __ldg(logl + (int64_t)f * npix + qq);
-                const float xp = f == 0 ? last_l[qq] : __ldg(logl + (int64_t)(f - 1) * npix + qq);
-                const float v = xc - xp;
-                const float* wt = w0 + (dy * ks0 + dx) * CP + c0;
-#pragma unroll
-                for (int c = 0; c < kHalf; ++c) acc[c] = fmaf(wt[c], v, acc[c]);
-              }
-            }
-          } else {
-            const float xc = __ldg(logl + (int64_t)f * npix + q);
-            const float xp = f == 0 ? last_l[q] : __ldg(logl + (int64_t)(f - 1) * npix + q);
-            xh[ring_pos(s0 + j, R) * TP + p] = xc - xp;
-            for (int tau0 = 0; tau0 < kt; ++tau0) {
-              const float v = xh[ring_pos(s0 + j - hk + tau0, R) * TP + p];
-              const float* wt = w0 + tau0 * CP + c0;
+        } else if (ks0 > 0) {
+          const int r0 = ks0 >> 1;
+          for (int dy = 0; dy < ks0; ++dy) {
+            const int yy = py + dy - r0;
+            if (yy < 0 || yy >= P.H) continue;
+            for (int dx = 0; dx < ks0; ++dx) {
+              const int xx = px + dx - r0;
+              if (xx < 0 || xx >= P.W) continue;
+              const int64_t qq = (int64_t)yy * P.W + xx;
+              const float xc = __ldg(logl + (int64_t)f * npix + qq);
+              const float xp = f == 0 ? last_l[qq] : __ldg(logl + (int64_t)(f - 1) * npix + qq);
+              const float v = xc - xp;
+              const float* wt = w0 + (dy * ks0 + dx) * CP + c0;
 #pragma unroll
               for (int c = 0; c < kHalf; ++c) acc[c] = fmaf(wt[c], v, acc[c]);
             }
           }
-        }
+        } else {
+          const float xc = __ldg(logl + (int64_t)f * npix + q);
+          const float xp = f == 0 ? last_l[q] : __ldg(logl + (int64_t)(f - 1) * npix + q);
+          xh[ring_pos(s0 + j, R) * TP + p] = xc - xp;
+          for (int tau0 = 0; tau0 < kt; ++tau0) {
+            const float v = xh[ring_pos(s0 + j - hk + tau0, R) * TP + p];
+            const float* wt = w0 + tau0 * CP + c0;
 #pragma unroll
-        for (int c = 0; c < kHalf; ++c) h0[j][c] = live ? fmaxf(acc[c], 0.0f) : 0.0f;
-        const int pj = pc + j >= R ? pc + j - R : pc + j;
-        store_half(slot_of(1, pj), hc, p, h0[j]);
+            for (int c = 0; c < kHalf; ++c) acc[c] = fmaf(wt[c], v, acc[c]);
+          }
+        }
       }
-      // the block input of the first residual block, kept FP32 for its closing layer
-      if (residual && L >= 3) {
-        tmem_st8x2(hb_col(0, tau & 1), hb_col(0, tau & 1) + CP, h0[0], h0[1]);
-      }
-      if (ks0 == 3 && !P.tma) load_x9(s0 + kT);   // next chunk's inputs, consumed next round
-      }
+#pragma unroll
+      for (int c = 0; c < kHalf; ++c) h0n[j][c] = live ? fmaxf(acc[c], 0.0f) : 0.0f;
     }
+  };
+  // chunk ch's layer-0 output into layer 1's ring, and (residual form) the
+  // first block's FP32 input into TMEM for its closing layer
+  auto stem_store = [&](int ch) {
+    const int pc = ring_pos(ch * kT, R), tc = min(kT, S - ch * kT);
+#pragma unroll
+    for (int j = 0; j < kT; ++j) {
+      if (j >= tc) break;
+      const int pj = pc + j >= R ? pc + j - R : pc + j;
+      store_half(slot_of(1, pj), hc, p, h0n[j]);
+    }
+    if (residual && L >= 3) tmem_st8x2(hb_col(0, ch & 1), hb_col(0, ch & 1) + CP, h0n[0], h0n[1]);
+  };
+  // chunk 0 before the first round (its previous frame may be the state's:
+  // thread loads), chunk 1's box in flight
+  if (tid == kIssuer && P.tma && nch > 1) issue_box(1);
+  if (worker && nch > 0) {
+    stem(0);
+    stem_store(0);
+    if (ks0 == 3 && !P.tma) load_x9(kT);
+  }
+  // Rounds: in round tau tensor-core layer l computes chunk tau - l + 1 and
+  // layer 0 chunk tau + 1, so that one MMA issue, one barrier and one pass of
+  // epilogues serve every layer, and layer 0's CUDA-core work runs while the
+  // MMAs do.  Layer l's epilogue writes chunk tau - l + 1 into layer l + 1's
+  // ring, over the slots that layer l + 1's MMAs of the same round read: the
+  // MMAs are issued last layer first and each epilogue waits for its own
+  // layer's commit, which follows every later layer's MMAs; layer 0's output
+  // is stored after layer 1's epilogue, the round's last.
+  for (int tau = 0; tau < nch + L - 2; ++tau) {
     // ---- every tensor-core layer's MMAs, last layer first
     fence_proxy_async_smem();
     tc_fence_before();
@@ -350,12 +375,10 @@ evsnet_tct_kernel(const __grid_constant__ CUtensorMap tmap, TctParams P, const f
     tc_fence_after();
     if (bail) break;
     if (tid == kIssuer) {
-      if (P.tma && tau + 1 < nch) {
-        // the next chunk's stem input (this chunk's was read before the barrier
-        // above, and every thread's proxy fence orders those reads first)
-        mbar_arrive_expect_tx(&tma_bar, kBoxBytes);
-        tma_load_3d(xbuf, &tmap, tx0 - 4, ty0 - 1, P.f0 + (tau + 1) * kT - 1, &tma_bar);
-      }
+      // the box of chunk tau + 2, into the buffer chunk tau's layer 0 read in
+      // the previous round (every thread's proxy fence before the barrier above
+      // orders those reads first)
+      if (P.tma && tau + 2 < nch) issue_box(tau + 2);
       constexpr uint64_t kBlock = (CP * 16) >> 4;   // one 16-row block of the strip
       constexpr uint64_t kSlotU = kSlot >> 4;
       // layer l's chunk this round starts at step 2 (tau - l + 1); its first
@@ -390,7 +413,11 @@ evsnet_tct_kernel(const __grid_constant__ CUtensorMap tmap, TctParams P, const f
         umma_commit(&lbar[l]);
       }
     }
-    if (P.tma && tau + 1 < nch) tma_pending = true;
+    // ---- layer 0 of the next chunk, in registers, while the MMAs run
+    if (worker && tau + 1 < nch) {
+      stem(tau + 1);
+      if (ks0 == 3 && !P.tma) load_x9((tau + 2) * kT);   // consumed next round
+    }
     // ---- epilogues, last layer first, each after its own layer's commit
     for (int l = L - 1; l >= 1 && worker; --l) {
       const int c = tau - l + 1;
@@ -463,6 +490,9 @@ evsnet_tct_kernel(const __grid_constant__ CUtensorMap tmap, TctParams P, const f
         }
       }
     }
+    // layer 1's MMAs of this round are complete: chunk tau + 1 may overwrite
+    // the ring slots they read
+    if (worker && tau + 1 < nch) stem_store(tau + 1);
     tmem_wait_st();
     tc_fence_before();
   }
@@ -472,7 +502,9 @@ evsnet_tct_kernel(const __grid_constant__ CUtensorMap tmap, TctParams P, const f
     // flight; wait for it, and for the TMA, with a second bounded wait
     if (tid == kIssuer) umma_commit(&drain_bar);
     mbar_wait(&drain_bar, 0, kDrainIters);
-    if (tma_pending) mbar_wait(&tma_bar, tma_phase, kDrainIters);
+    if (tid == kIssuer)
+      for (int b = 0; b < 2; ++b)
+        if (tma_issued[b] > 0) mbar_wait(&tma_bar[b], (uint32_t)((tma_issued[b] - 1) & 1), kDrainIters);
   } else if (live) {
     if (hc == 0) Vg[q] = V;
     // the last kt - 1 inputs of every layer back to the state, oldest first
@@ -528,7 +560,7 @@ int et_evsnet_forward_tct(const float* logl, int32_t F, const et_evsnet_weights*
   std::memset(&tmap, 0, sizeof(tmap));
   P.tma = P.ks0 == 3 && P.W % TP == 0 && (reinterpret_cast<uintptr_t>(logl) & 15) == 0 && F >= 1;
   P.off_xbuf = (int)(((size_t)P.off_f32 + fbytes + 127) & ~(size_t)127);
-  const size_t smem = (size_t)P.off_xbuf + (P.tma ? (size_t)kBoxBytes : 0);
+  const size_t smem = (size_t)P.off_xbuf + (P.tma ? (size_t)(kBoxStride + kBoxFloats) * 4 : 0);
   if (P.tma) {
     typedef CUresult (*EncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
