@@ -6,11 +6,12 @@
 // residual sums, the projection and BiLIF stay FP32.
 //
 // A CTA owns a tile of 128 consecutive pixels for the whole call: one TMEM
-// lane per pixel and two threads per pixel (warps w and w + 4 share TMEM lane
-// quarter w), each owning 8 of the 16 channels -- its 8 accumulator columns,
-// one 16-byte plane row of the operands and half of every epilogue -- plus a
-// ninth warp whose one thread issues every MMA and TMA copy, so that issuing
-// never holds up the epilogues.  The input history of every layer >= 1 (its
+// lane per pixel and four threads per pixel (warps w, w + 4, w + 8, w + 12
+// share TMEM lane quarter w), each owning one step of a chunk and 8 of the 16
+// channels -- its 8 accumulator columns, one 16-byte plane row of the
+// operands and a quarter of every epilogue -- plus a seventeenth warp whose
+// one thread issues every MMA and TMA copy, so that issuing never holds up
+// the epilogues.  The input history of every layer >= 1 (its
 // last kt inputs) lives in shared memory as a ring of kt + kT - 1 slots, each
 // slot one step of 128 pixels x 16 channels in the K-major, no-swizzle operand
 // layout (two 2 KB planes of 8 channels, 16-byte rows), so the A operand of tap
@@ -71,14 +72,17 @@ constexpr int kMaxStem = 7;
 constexpr int kSlot = TP * CP * 2;      // bytes of one ring slot
 constexpr int kPlane = TP * 16;         // bytes of 8 channels of 128 rows
 constexpr int kHalf = CP / 2;            // channels per thread
-constexpr int kWorkers = 2 * TP;       // two threads per pixel
+constexpr int kWorkers = 4 * TP;       // four threads per pixel: (step of the chunk, channel half)
 constexpr int kThreads = kWorkers + 32; // and one warp that issues the MMAs and the TMA copies
 constexpr int kIssuer = kWorkers;       // its issuing thread
 // TMEM: kT x 16 accumulator columns per tensor-core layer, then the FP32
 // block inputs of up to three residual blocks for two chunks
 constexpr int kHbCol = (kMaxLayers - 1) * kT * 16;
 constexpr uint32_t kTmemCols = 512;
-static_assert(kHbCol + 3 * 2 * kT * 16 <= (int)kTmemCols, "TMEM columns");
+// then the projection's partial sums of a pixel's other three threads (one
+// column each, 8 apart)
+constexpr int kPartCol = kHbCol + 3 * 2 * kT * 16;
+static_assert(kPartCol + 24 <= (int)kTmemCols, "TMEM columns");
 constexpr unsigned long long kTimeoutBit = 1ull << 62;
 constexpr uint32_t kDrainIters = 1u << 22;   // bound of the waits for work in flight after a bail
 
@@ -147,11 +151,12 @@ evsnet_tct_kernel(const __grid_constant__ CUtensorMap tmap, TctParams P, const f
   __shared__ uint64_t drain_bar;
   __shared__ uint32_t tmem_slot;
   __shared__ int bail;
-  __shared__ float part[kT][TP];        // the second half's share of the projection
   const int L = P.L, C = P.C, kt = P.kt, R = P.R, hk = kt - 1, ks0 = P.ks0;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int p = tid & (TP - 1);         // pixel of the tile = TMEM lane
-  const int hc = tid >> 7;              // channel half: channels 8 hc .. 8 hc + 7
+  const int grp = tid >> 7;             // thread group of the pixel: (js, hc)
+  const int js = grp >> 1;              // step of the chunk this thread computes
+  const int hc = grp & 1;               // channel half: channels 8 hc .. 8 hc + 7
   const int c0 = hc * kHalf;
   const int64_t npix = (int64_t)P.H * P.W;
   const int64_t q = (int64_t)blockIdx.x * TP + p;
@@ -196,22 +201,28 @@ evsnet_tct_kernel(const __grid_constant__ CUtensorMap tmap, TctParams P, const f
   }
   // ring slots of steps -(kt-1) .. -1 from the state (oldest first); a
   // layer's loads are all issued before its stores
+  // (the two step groups take alternate slots)
   for (int l = 1; l < L; ++l) {
-    float v[kMaxKt - 1][kHalf];
+    constexpr int kJ = kMaxKt / 2;
+    float v[kJ][kHalf];
 #pragma unroll
-    for (int j = 0; j < kMaxKt - 1; ++j)
+    for (int jj = 0; jj < kJ; ++jj) {
+      const int j = 2 * jj + js;
 #pragma unroll
       for (int c = 0; c < kHalf; ++c)
-        v[j][c] = (j < hk && live && c0 + c < C) ? hist[hidx(l, j, c0 + c)] : 0.0f;
+        v[jj][c] = (j < hk && live && c0 + c < C) ? hist[hidx(l, j, c0 + c)] : 0.0f;
+    }
 #pragma unroll
-    for (int j = 0; j < kMaxKt - 1; ++j)
-      if (worker && j < hk) store_half(slot_of(l, ring_pos(j - hk, R)), hc, p, v[j]);
+    for (int jj = 0; jj < kJ; ++jj) {
+      const int j = 2 * jj + js;
+      if (worker && j < hk) store_half(slot_of(l, ring_pos(j - hk, R)), hc, p, v[jj]);
+    }
   }
   if (ks0 == 0 && worker) {
-    // both halves write the same values: each reads back its own writes
+    // all four threads of the pixel write the same values: each reads back its own writes
     for (int j = 0; j < hk; ++j) xh[ring_pos(j - hk, R) * TP + p] = live ? hist[hidx(0, j, 0)] : 0.0f;
   }
-  float V = (live && hc == 0) ? Vg[q] : 0.0f;
+  float V = (live && grp == 0) ? Vg[q] : 0.0f;
   if (warp == 0) tmem_alloc(&tmem_slot, kTmemCols);
   if (tid == 0) {
     for (int l = 0; l < kMaxLayers; ++l) mbar_init(&lbar[l], 1);
@@ -237,22 +248,19 @@ evsnet_tct_kernel(const __grid_constant__ CUtensorMap tmap, TctParams P, const f
 
   const int S = P.F - P.f0;             // steps of this call
   const int nch = (S + kT - 1) / kT;    // chunks of kT steps
-  // 3 x 3 stem: the nine neighbours' X of the steps of a chunk, loaded one
-  // chunk ahead so that their latency hides behind the tensor-core layers
-  float xn[kT][9];
+  // 3 x 3 stem: the nine neighbours' X of this thread's step of a chunk,
+  // loaded a chunk ahead so that their latency hides behind the tensor-core layers
+  float xn[9];
   auto load_x9 = [&](int s_first) {
+    const int f = P.f0 + s_first + js;
 #pragma unroll
-    for (int j = 0; j < kT; ++j) {
-      const int f = P.f0 + s_first + j;
-#pragma unroll
-      for (int t = 0; t < 9; ++t) {
-        const int yy = py + t / 3 - 1, xx = px + t % 3 - 1;
-        const bool in = live && s_first + j < S && yy >= 0 && yy < P.H && xx >= 0 && xx < P.W;
-        const int64_t qq = in ? (int64_t)yy * P.W + xx : 0;
-        const float xc = in ? __ldg(logl + (int64_t)f * npix + qq) : 0.0f;
-        const float xp = !in ? 0.0f : (f == 0 ? last_l[qq] : __ldg(logl + (int64_t)(f - 1) * npix + qq));
-        xn[j][t] = xc - xp;
-      }
+    for (int t = 0; t < 9; ++t) {
+      const int yy = py + t / 3 - 1, xx = px + t % 3 - 1;
+      const bool in = live && s_first + js < S && yy >= 0 && yy < P.H && xx >= 0 && xx < P.W;
+      const int64_t qq = in ? (int64_t)yy * P.W + xx : 0;
+      const float xc = in ? __ldg(logl + (int64_t)f * npix + qq) : 0.0f;
+      const float xp = !in ? 0.0f : (f == 0 ? last_l[qq] : __ldg(logl + (int64_t)(f - 1) * npix + qq));
+      xn[t] = xc - xp;
     }
   };
   if (ks0 == 3) load_x9(0);
@@ -267,10 +275,10 @@ evsnet_tct_kernel(const __grid_constant__ CUtensorMap tmap, TctParams P, const f
     tma_load_3d(xbuf + b * kBoxStride, &tmap, tx0 - 4, ty0 - 1, P.f0 + ch * kT - 1, &tma_bar[b]);
     ++tma_issued[b];
   };
-  // layer 0 on CUDA cores, FP32, of chunk ch into h0n: X_k = l_k - l_{k-1}
-  // (Eq. 1); the 3 x 3 stem reads its neighbours' X from xn (thread loads)
-  // or from the chunk's TMA box
-  float h0n[kT][kHalf];
+  // layer 0 on CUDA cores, FP32, of this thread's step of chunk ch into h0n:
+  // X_k = l_k - l_{k-1} (Eq. 1); the 3 x 3 stem reads its neighbours' X from
+  // xn (thread loads) or from the chunk's TMA box
+  float h0n[kHalf];
   auto stem = [&](int ch) {
     const int s0 = ch * kT, tc = min(kT, S - s0);
     if (P.tma && ch > 0) {
@@ -282,74 +290,71 @@ evsnet_tct_kernel(const __grid_constant__ CUtensorMap tmap, TctParams P, const f
       tma_phase[b] ^= 1u;
       const float* xb = xbuf + b * kBoxStride;
 #pragma unroll
-      for (int j = 0; j < kT; ++j)
-#pragma unroll
-        for (int t = 0; t < 9; ++t) {
-          const int col = p + t % 3 + 3, row = t / 3;
-          xn[j][t] = xb[((1 + j) * 3 + row) * kBoxW + col] - xb[(j * 3 + row) * kBoxW + col];
-        }
+      for (int t = 0; t < 9; ++t) {
+        const int col = p + t % 3 + 3, row = t / 3;
+        xn[t] = xb[((1 + js) * 3 + row) * kBoxW + col] - xb[(js * 3 + row) * kBoxW + col];
+      }
+    }
+    if (ks0 == 0 && live) {
+      // the temporal layer 0's X ring: every thread of the pixel writes both
+      // steps (the same values), so that each reads back its own writes
+      for (int j = 0; j < tc; ++j) {
+        const int f = P.f0 + s0 + j;
+        const float xc = __ldg(logl + (int64_t)f * npix + q);
+        const float xp = f == 0 ? last_l[q] : __ldg(logl + (int64_t)(f - 1) * npix + q);
+        xh[ring_pos(s0 + j, R) * TP + p] = xc - xp;
+      }
     }
 #pragma unroll
-    for (int j = 0; j < kT; ++j) {
+    for (int c = 0; c < kHalf; ++c) h0n[c] = 0.0f;
+    if (js >= tc) return;
+    const int f = P.f0 + s0 + js;
+    float acc[kHalf];
 #pragma unroll
-      for (int c = 0; c < kHalf; ++c) h0n[j][c] = 0.0f;
-      if (j >= tc) continue;
-      const int f = P.f0 + s0 + j;
-      float acc[kHalf];
+    for (int c = 0; c < kHalf; ++c) acc[c] = bs[c0 + c];
+    if (live) {
+      if (ks0 == 3) {
 #pragma unroll
-      for (int c = 0; c < kHalf; ++c) acc[c] = bs[c0 + c];
-      if (live) {
-        if (ks0 == 3) {
+        for (int t = 0; t < 9; ++t) {
+          const float* wt = w0 + t * CP + c0;
 #pragma unroll
-          for (int t = 0; t < 9; ++t) {
-            const float* wt = w0 + t * CP + c0;
-#pragma unroll
-            for (int c = 0; c < kHalf; ++c) acc[c] = fmaf(wt[c], xn[j][t], acc[c]);
-          }
-        } else if (ks0 > 0) {
-          const int r0 = ks0 >> 1;
-          for (int dy = 0; dy < ks0; ++dy) {
-            const int yy = py + dy - r0;
-            if (yy < 0 || yy >= P.H) continue;
-            for (int dx = 0; dx < ks0; ++dx) {
-              const int xx = px + dx - r0;
-              if (xx < 0 || xx >= P.W) continue;
-              const int64_t qq = (int64_t)yy * P.W + xx;
-              const float xc = __ldg(logl + (int64_t)f * npix + qq);
-              const float xp = f == 0 ? last_l[qq] : __ldg(logl + (int64_t)(f - 1) * npix + qq);
-              const float v = xc - xp;
-              const float* wt = w0 + (dy * ks0 + dx) * CP + c0;
-#pragma unroll
-              for (int c = 0; c < kHalf; ++c) acc[c] = fmaf(wt[c], v, acc[c]);
-            }
-          }
-        } else {
-          const float xc = __ldg(logl + (int64_t)f * npix + q);
-          const float xp = f == 0 ? last_l[q] : __ldg(logl + (int64_t)(f - 1) * npix + q);
-          xh[ring_pos(s0 + j, R) * TP + p] = xc - xp;
-          for (int tau0 = 0; tau0 < kt; ++tau0) {
-            const float v = xh[ring_pos(s0 + j - hk + tau0, R) * TP + p];
-            const float* wt = w0 + tau0 * CP + c0;
+          for (int c = 0; c < kHalf; ++c) acc[c] = fmaf(wt[c], xn[t], acc[c]);
+        }
+      } else if (ks0 > 0) {
+        const int r0 = ks0 >> 1;
+        for (int dy = 0; dy < ks0; ++dy) {
+          const int yy = py + dy - r0;
+          if (yy < 0 || yy >= P.H) continue;
+          for (int dx = 0; dx < ks0; ++dx) {
+            const int xx = px + dx - r0;
+            if (xx < 0 || xx >= P.W) continue;
+            const int64_t qq = (int64_t)yy * P.W + xx;
+            const float xc = __ldg(logl + (int64_t)f * npix + qq);
+            const float xp = f == 0 ? last_l[qq] : __ldg(logl + (int64_t)(f - 1) * npix + qq);
+            const float v = xc - xp;
+            const float* wt = w0 + (dy * ks0 + dx) * CP + c0;
 #pragma unroll
             for (int c = 0; c < kHalf; ++c) acc[c] = fmaf(wt[c], v, acc[c]);
           }
         }
+      } else {
+        for (int tau0 = 0; tau0 < kt; ++tau0) {
+          const float v = xh[ring_pos(s0 + js - hk + tau0, R) * TP + p];
+          const float* wt = w0 + tau0 * CP + c0;
+#pragma unroll
+          for (int c = 0; c < kHalf; ++c) acc[c] = fmaf(wt[c], v, acc[c]);
+        }
       }
-#pragma unroll
-      for (int c = 0; c < kHalf; ++c) h0n[j][c] = live ? fmaxf(acc[c], 0.0f) : 0.0f;
     }
+#pragma unroll
+    for (int c = 0; c < kHalf; ++c) h0n[c] = live ? fmaxf(acc[c], 0.0f) : 0.0f;
   };
-  // chunk ch's layer-0 output into layer 1's ring, and (residual form) the
-  // first block's FP32 input into TMEM for its closing layer
+  // this thread's step of chunk ch into layer 1's ring, and (residual form)
+  // the first block's FP32 input into TMEM for its closing layer
   auto stem_store = [&](int ch) {
-    const int pc = ring_pos(ch * kT, R), tc = min(kT, S - ch * kT);
-#pragma unroll
-    for (int j = 0; j < kT; ++j) {
-      if (j >= tc) break;
-      const int pj = pc + j >= R ? pc + j - R : pc + j;
-      store_half(slot_of(1, pj), hc, p, h0n[j]);
-    }
-    if (residual && L >= 3) tmem_st8x2(hb_col(0, ch & 1), hb_col(0, ch & 1) + CP, h0n[0], h0n[1]);
+    const int s0 = ch * kT, tc = min(kT, S - s0);
+    if (js < tc) store_half(slot_of(1, ring_pos(s0 + js, R)), hc, p, h0n);
+    if (residual && L >= 3) tmem_st8(hb_col(0, ch & 1) + js * CP, h0n);
   };
   // chunk 0 before the first round (its previous frame may be the state's:
   // thread loads), chunk 1's box in flight
@@ -431,41 +436,41 @@ evsnet_tct_kernel(const __grid_constant__ CUtensorMap tmap, TctParams P, const f
       lphase ^= 1u << l;
       tc_fence_after();
       const bool closing = residual && (l % 2) == 0;
-      const bool inner = residual && (l % 2) == 1;
-      float accs[kT][kHalf], hin[kT][kHalf];
-      tmem_ld8x2(acc_col(l), acc_col(l) + CP, accs[0], accs[1]);
-      if (closing) tmem_ld8x2(hb_col(l / 2 - 1, c & 1), hb_col(l / 2 - 1, c & 1) + CP, hin[0], hin[1]);
-      float out[kT][kHalf];
+      // this thread's step and channel half of the accumulators (and of the
+      // block input for a closing layer)
+      float acc[kHalf], hin[kHalf];
+      if (closing) tmem_ld8x2(acc_col(l) + js * CP, hb_col(l / 2 - 1, c & 1) + js * CP, acc, hin);
+      else tmem_ld8(acc_col(l) + js * CP, acc);
+      float out[kHalf];
 #pragma unroll
-      for (int j = 0; j < kT; ++j)
-#pragma unroll
-        for (int c2 = 0; c2 < kHalf; ++c2) {
-          const float v = accs[j][c2] + bs[l * CP + c0 + c2];
-          float o = closing ? fmaxf(hin[j][c2] + v, 0.0f) : fmaxf(v, 0.0f);
-          out[j][c2] = (live && j < tc) ? o : 0.0f;
-        }
-      (void)inner;
+      for (int c2 = 0; c2 < kHalf; ++c2) {
+        const float v = acc[c2] + bs[l * CP + c0 + c2];
+        const float o = closing ? fmaxf(hin[c2] + v, 0.0f) : fmaxf(v, 0.0f);
+        out[c2] = (live && js < tc) ? o : 0.0f;
+      }
       if (l + 1 < L) {
-#pragma unroll
-        for (int j = 0; j < kT; ++j) {
-          if (j >= tc) break;
-          const int pj = pc + j >= R ? pc + j - R : pc + j;
-          store_half(slot_of(l + 1, pj), hc, p, out[j]);
-        }
+        if (js < tc) store_half(slot_of(l + 1, pc + js >= R ? pc + js - R : pc + js), hc, p, out);
         // a closing layer's output is the next block's input
-        if (closing && l + 2 < L) tmem_st8x2(hb_col(l / 2, c & 1), hb_col(l / 2, c & 1) + CP, out[0], out[1]);
+        if (closing && l + 2 < L) tmem_st8(hb_col(l / 2, c & 1) + js * CP, out);
       } else {
-        // ---- Eq. 6 projection (each half its 8 channels) and BiLIF, step by step
+        // ---- Eq. 6 projection and BiLIF, step by step: the partial sums of
+        // the pixel's other three threads reach thread group 0 through TMEM
+        // (the pixel's own lane, one column each)
+        float Ih = hc == 0 ? bp[0] : 0.0f;
 #pragma unroll
-        for (int j = 0; j < kT; ++j) {
-          if (j >= tc) break;
-          float Ih = hc == 0 ? bp[0] : 0.0f;
-#pragma unroll
-          for (int c2 = 0; c2 < kHalf; ++c2) Ih = fmaf(wp[c0 + c2], out[j][c2], Ih);
-          if (hc == 1) part[j][p] = Ih;
+        for (int c2 = 0; c2 < kHalf; ++c2) Ih = fmaf(wp[c0 + c2], out[c2], Ih);
+        if (grp > 0) {
+          tmem_st1(tmem + lane_base + (uint32_t)(kPartCol + 8 * (grp - 1)), Ih);
+          tmem_wait_st();
         }
+        tc_fence_before();
         workers_sync();
-        if (hc == 0) {
+        tc_fence_after();
+        if (grp == 0) {
+          float p01, p10, p11;   // (step, half) = (0, 1), (1, 0), (1, 1)
+          tmem_ld1x3(tmem + lane_base + (uint32_t)kPartCol, tmem + lane_base + (uint32_t)(kPartCol + 8),
+                     tmem + lane_base + (uint32_t)(kPartCol + 16), p01, p10, p11);
+          const float Is[kT] = {Ih + p01, p10 + p11};
 #pragma unroll
           for (int j = 0; j < kT; ++j) {
             if (j >= tc) break;
@@ -473,10 +478,7 @@ evsnet_tct_kernel(const __grid_constant__ CUtensorMap tmap, TctParams P, const f
             uint32_t nev = 0;
             int Sp = 0;
             if (live) {
-              float I = bp[0];
-#pragma unroll
-              for (int c2 = 0; c2 < kHalf; ++c2) I = fmaf(wp[c2], out[j][c2], I);
-              I += part[j][p];
+              const float I = Is[j];
               const float vp = P.beta * V + I;
               Sp = vp >= P.vth ? 1 : (vp <= -P.vth ? -1 : 0);
               V = vp - P.reset * (float)Sp;
@@ -506,16 +508,17 @@ evsnet_tct_kernel(const __grid_constant__ CUtensorMap tmap, TctParams P, const f
       for (int b = 0; b < 2; ++b)
         if (tma_issued[b] > 0) mbar_wait(&tma_bar[b], (uint32_t)((tma_issued[b] - 1) & 1), kDrainIters);
   } else if (live) {
-    if (hc == 0) Vg[q] = V;
+    if (grp == 0) Vg[q] = V;
     // the last kt - 1 inputs of every layer back to the state, oldest first
+    // (the two step groups take alternate slots)
     for (int l = 1; l < L; ++l)
-      for (int j = 0; j < hk; ++j) {
+      for (int j = js; j < hk; j += 2) {
         float v[kHalf];
         load_half(slot_of(l, ring_pos(S - hk + j, R)), hc, p, v);
         for (int c = 0; c < kHalf; ++c)
           if (c0 + c < C) hist[hidx(l, j, c0 + c)] = v[c];
       }
-    if (ks0 == 0 && hc == 0)
+    if (ks0 == 0 && grp == 0)
       for (int j = 0; j < hk; ++j) hist[hidx(0, j, 0)] = xh[ring_pos(S - hk + j, R) * TP + p];
   }
   tc_fence_before();
@@ -586,8 +589,10 @@ int et_evsnet_forward_tct(const float* logl, int32_t F, const et_evsnet_weights*
   int dev = 0, max_smem = 0;
   ET_CHECK_CUDA(cudaGetDevice(&dev));
   ET_CHECK_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  // static shared memory (barrier, TMEM slot, flag) comes on top of the dynamic part
-  if (smem + 2048 > (size_t)max_smem) return ET_ERR_UNIMPLEMENTED;
+  // static shared memory (barriers, TMEM slot, flag) comes on top of the dynamic part
+  cudaFuncAttributes fa;
+  ET_CHECK_CUDA(cudaFuncGetAttributes(&fa, evsnet_tct_kernel));
+  if (smem + fa.sharedSizeBytes > (size_t)max_smem) return ET_ERR_UNIMPLEMENTED;
   if (P.kt > 1 && !st->hist) return ET_ERR_ARG;
   ET_CHECK_CUDA(cudaFuncSetAttribute(evsnet_tct_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int64_t npix = (int64_t)P.H * P.W;

@@ -163,3 +163,35 @@ __device__ __forceinline__ void tmem_st8x2(uint32_t taddr0, uint32_t taddr1, con
       : "memory");
 }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// 32 lanes x 8 consecutive 32-bit TMEM columns from 8 registers per thread;
+// complete after tmem_wait_st.
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const float* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+      "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+      "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
+      : "memory");
+}
+
+// 32 lanes x one 32-bit TMEM column: store (complete after tmem_wait_st), and
+// three single-column loads completed by one wait inside the same statement
+__device__ __forceinline__ void tmem_st1(uint32_t taddr, float v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x1.b32 [%0], {%1};" ::"r"(taddr), "r"(__float_as_uint(v))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld1x3(uint32_t t0, uint32_t t1, uint32_t t2, float& a, float& b, float& c) {
+  uint32_t r0, r1, r2;
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%3];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x1.b32 {%1}, [%4];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x1.b32 {%2}, [%5];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r0), "=r"(r1), "=r"(r2)
+      : "r"(t0), "r"(t1), "r"(t2)
+      : "memory");
+  a = __uint_as_float(r0);
+  b = __uint_as_float(r1);
+  c = __uint_as_float(r2);
+}
