@@ -569,7 +569,8 @@ def event_gate(api, inputs, g, net, dev, stream, s0, nb, spp, W, H, warm=64, n_1
     out["ceiling_1024spp_render"] = _f1s(api, _win(_thr(api, lq, s0, dev), lo, s0 + n_1024), r_short
                                          if n_1024 == n_thr else _win(ref_ev, lo, s0 + n_1024))
     out["ceiling_1024spp_frames"] = n_1024
-    out["gate_0.9_met"] = out["method"][1] >= 0.9
+    # an empty scoring window (too few frames for the delay) decides nothing
+    out["gate_0.9_met"] = (out["method"][1] >= 0.9) if out["n_ref"] > 0 else None
     return out
 
 
