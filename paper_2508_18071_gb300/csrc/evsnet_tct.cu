@@ -6,10 +6,11 @@
 // residual sums, the projection and BiLIF stay FP32.
 //
 // A CTA owns a tile of 128 consecutive pixels for the whole call: one TMEM
-// lane per pixel and four threads per pixel (warps w, w + 4, w + 8, w + 12
-// share TMEM lane quarter w), each owning one step of a chunk and 8 of the 16
-// channels -- its 8 accumulator columns, one 16-byte plane row of the
-// operands and a quarter of every epilogue -- plus a seventeenth warp whose
+// lane per pixel and three groups of 128 threads, one thread per pixel each
+// (warps w, w + 4, w + 8 share TMEM lane quarter w); group g runs the
+// epilogues of every third tensor-core layer counting down from the last, so
+// that consecutive layers' epilogues run at once in different warps; group 2
+// also runs layer 0, group 0 the projection and BiLIF.  A thirteenth warp's
 // one thread issues every MMA and TMA copy, so that issuing never holds up
 // the epilogues.  The input history of every layer >= 1 (its
 // last kt inputs) lives in shared memory as a ring of kt + kT - 1 slots, each
@@ -71,18 +72,17 @@ constexpr int kMaxKt = 7;
 constexpr int kMaxStem = 7;
 constexpr int kSlot = TP * CP * 2;      // bytes of one ring slot
 constexpr int kPlane = TP * 16;         // bytes of 8 channels of 128 rows
-constexpr int kHalf = CP / 2;            // channels per thread
-constexpr int kWorkers = 4 * TP;       // four threads per pixel: (step of the chunk, channel half)
+constexpr int kHalf = CP / 2;            // channels of one operand plane
+constexpr int kGroups = 3;              // worker groups, one thread per pixel each
+constexpr int kStemGroup = kGroups - 1; // the group that also runs layer 0
+constexpr int kWorkers = kGroups * TP;
 constexpr int kThreads = kWorkers + 32; // and one warp that issues the MMAs and the TMA copies
 constexpr int kIssuer = kWorkers;       // its issuing thread
 // TMEM: kT x 16 accumulator columns per tensor-core layer, then the FP32
-// block inputs of up to three residual blocks for two chunks
+// block inputs of up to three residual blocks for three chunks
 constexpr int kHbCol = (kMaxLayers - 1) * kT * 16;
 constexpr uint32_t kTmemCols = 512;
-// then the projection's partial sums of a pixel's other three threads (one
-// column each, 8 apart)
-constexpr int kPartCol = kHbCol + 3 * 2 * kT * 16;
-static_assert(kPartCol + 24 <= (int)kTmemCols, "TMEM columns");
+static_assert(kHbCol + 3 * 3 * kT * 16 <= (int)kTmemCols, "TMEM columns");
 constexpr unsigned long long kTimeoutBit = 1ull << 62;
 constexpr uint32_t kDrainIters = 1u << 22;   // bound of the waits for work in flight after a bail
 
@@ -106,9 +106,6 @@ constexpr int kBoxStride = (kBoxFloats + 31) / 32 * 32;
 
 __device__ __forceinline__ int ring_pos(int s, int R) { return ((s % R) + R) % R; }
 
-// barrier of the pixel warps only (the issuing warp does not take part)
-__device__ __forceinline__ void workers_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kWorkers) : "memory"); }
-
 // two floats as one 32-bit word of BF16 (round to nearest even), low half first
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
@@ -121,11 +118,13 @@ __device__ __forceinline__ float2 unpack_bf16(uint32_t w) {
   return __bfloat1622float2(h);
 }
 
-// 8 channels of one pixel, BF16-rounded, as row `m` of plane `hc` of a ring
-// slot (plane 0: channels 0-7, plane 1: channels 8-15)
-__device__ __forceinline__ void store_half(unsigned char* slot, int hc, int m, const float (&v)[kHalf]) {
-  *reinterpret_cast<uint4*>(slot + hc * kPlane + m * 16) =
+// all 16 channels of one pixel, BF16-rounded, as row m of a ring slot (plane
+// 0: channels 0-7, plane 1: channels 8-15), and back
+__device__ __forceinline__ void store_row(unsigned char* slot, int m, const float* v) {
+  *reinterpret_cast<uint4*>(slot + m * 16) =
       make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
+  *reinterpret_cast<uint4*>(slot + kPlane + m * 16) =
+      make_uint4(pack_bf16(v[8], v[9]), pack_bf16(v[10], v[11]), pack_bf16(v[12], v[13]), pack_bf16(v[14], v[15]));
 }
 
 __device__ __forceinline__ void load_half(const unsigned char* slot, int hc, int m, float (&v)[kHalf]) {
@@ -136,6 +135,17 @@ __device__ __forceinline__ void load_half(const unsigned char* slot, int hc, int
     const float2 f = unpack_bf16(w[i]);
     v[2 * i] = f.x;
     v[2 * i + 1] = f.y;
+  }
+}
+
+__device__ __forceinline__ void load_row(const unsigned char* slot, int m, float (&v)[CP]) {
+  float lo[kHalf], hi[kHalf];
+  load_half(slot, 0, m, lo);
+  load_half(slot, 1, m, hi);
+#pragma unroll
+  for (int c = 0; c < kHalf; ++c) {
+    v[c] = lo[c];
+    v[kHalf + c] = hi[c];
   }
 }
 
@@ -154,13 +164,15 @@ evsnet_tct_kernel(const __grid_constant__ CUtensorMap tmap, TctParams P, const f
   const int L = P.L, C = P.C, kt = P.kt, R = P.R, hk = kt - 1, ks0 = P.ks0;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int p = tid & (TP - 1);         // pixel of the tile = TMEM lane
-  const int grp = tid >> 7;             // thread group of the pixel: (js, hc)
-  const int js = grp >> 1;              // step of the chunk this thread computes
-  const int hc = grp & 1;               // channel half: channels 8 hc .. 8 hc + 7
-  const int c0 = hc * kHalf;
+  const int grp = tid >> 7;             // worker group (4 = the issuing warp)
+  // group g runs the epilogues of the tensor-core layers l with
+  // (L - 1 - l) % 3 == g (the last layer, with the projection and BiLIF, in
+  // group 0), so that consecutive layers' epilogues run in different warps
+  auto owns = [&](int l) { return (L - 1 - l) % kGroups == grp; };
   const int64_t npix = (int64_t)P.H * P.W;
   const int64_t q = (int64_t)blockIdx.x * TP + p;
   const bool worker = tid < kWorkers;
+  const bool stem_grp = grp == kStemGroup;
   const bool live = worker && q < npix;
   const int px = live ? (int)(q % P.W) : 0, py = live ? (int)(q / P.W) : 0;
   unsigned char* rings = sm;                                   // [L-1][R] slots
@@ -199,29 +211,28 @@ evsnet_tct_kernel(const __grid_constant__ CUtensorMap tmap, TctParams P, const f
                          ((kt - 1 - tau) * CP + n) * 16 + (k & 7) * 2;
     *reinterpret_cast<__nv_bfloat16*>(dst) = __float2bfloat16_rn(v);
   }
-  // ring slots of steps -(kt-1) .. -1 from the state (oldest first); a
-  // layer's loads are all issued before its stores
-  // (the two step groups take alternate slots)
+  // ring slots of steps -(kt-1) .. -1 from the state (oldest first): group g
+  // fills the slots j with j % 3 == g (both channel halves), a layer's loads
+  // issued before its stores
   for (int l = 1; l < L; ++l) {
-    constexpr int kJ = kMaxKt / 2;
-    float v[kJ][kHalf];
+    constexpr int kJ = (kMaxKt - 1 + kGroups - 1) / kGroups;
+    float v[kJ][CP];
 #pragma unroll
     for (int jj = 0; jj < kJ; ++jj) {
-      const int j = 2 * jj + js;
+      const int j = jj * kGroups + grp;
 #pragma unroll
-      for (int c = 0; c < kHalf; ++c)
-        v[jj][c] = (j < hk && live && c0 + c < C) ? hist[hidx(l, j, c0 + c)] : 0.0f;
+      for (int c = 0; c < CP; ++c) v[jj][c] = (j < hk && live && c < C) ? hist[hidx(l, j, c)] : 0.0f;
     }
 #pragma unroll
     for (int jj = 0; jj < kJ; ++jj) {
-      const int j = 2 * jj + js;
-      if (worker && j < hk) store_half(slot_of(l, ring_pos(j - hk, R)), hc, p, v[jj]);
+      const int j = jj * kGroups + grp;
+      if (worker && j < hk) {
+        store_row(slot_of(l, ring_pos(j - hk, R)), p, v[jj]);
+      }
     }
   }
-  if (ks0 == 0 && worker) {
-    // all four threads of the pixel write the same values: each reads back its own writes
+  if (ks0 == 0 && stem_grp)
     for (int j = 0; j < hk; ++j) xh[ring_pos(j - hk, R) * TP + p] = live ? hist[hidx(0, j, 0)] : 0.0f;
-  }
   float V = (live && grp == 0) ? Vg[q] : 0.0f;
   if (warp == 0) tmem_alloc(&tmem_slot, kTmemCols);
   if (tid == 0) {
@@ -239,35 +250,40 @@ evsnet_tct_kernel(const __grid_constant__ CUtensorMap tmap, TctParams P, const f
   const uint32_t idesc16 = umma_idesc_bf16(TP, CP), idesc32 = umma_idesc_bf16(TP, 2 * CP);
   const uint64_t a_desc0 = umma_desc(smem_u32(rings), kPlane, 128);
   const uint64_t b_desc0 = umma_desc(smem_u32(wB), kt * CP * 16, 128);
-  // TMEM columns: layer l's accumulators at 32 (l - 1); the FP32 block inputs
-  // of the residual form (block b, chunk parity) at kHbCol + 32 (2 b + parity)
-  auto acc_col = [&](int l) { return tmem + lane_base + (uint32_t)((l - 1) * kT * CP + c0); };
-  auto hb_col = [&](int b, int par) { return tmem + lane_base + (uint32_t)(kHbCol + (2 * b + par) * kT * CP + c0); };
-  uint32_t lphase = 0;                  // bit l: parity of the next completion of lbar[l]
+  // TMEM columns: layer l's accumulators (both steps, 16 channels each) at
+  // 32 (l - 1); the FP32 block inputs of the residual form (block b, chunk c)
+  // at kHbCol + 32 (3 b + c % 3): a block input written for chunk c + 2 never
+  // meets the one read for chunk c
+  auto acc_col = [&](int l) { return tmem + lane_base + (uint32_t)((l - 1) * kT * CP); };
+  auto hb_col = [&](int b, int c) { return tmem + lane_base + (uint32_t)(kHbCol + (3 * b + c % 3) * kT * CP); };
+  uint32_t lphase = 0;                  // bit l: parity of the next completion of lbar[l] this thread waits for
   const bool residual = P.kind == ET_NET_RESIDUAL;
 
   const int S = P.F - P.f0;             // steps of this call
   const int nch = (S + kT - 1) / kT;    // chunks of kT steps
-  // 3 x 3 stem: the nine neighbours' X of this thread's step of a chunk,
-  // loaded a chunk ahead so that their latency hides behind the tensor-core layers
-  float xn[9];
+  // 3 x 3 stem: the nine neighbours' X of the steps of a chunk, loaded a chunk
+  // ahead so that their latency hides behind the tensor-core layers
+  float xn[kT][9];
   auto load_x9 = [&](int s_first) {
-    const int f = P.f0 + s_first + js;
 #pragma unroll
-    for (int t = 0; t < 9; ++t) {
-      const int yy = py + t / 3 - 1, xx = px + t % 3 - 1;
-      const bool in = live && s_first + js < S && yy >= 0 && yy < P.H && xx >= 0 && xx < P.W;
-      const int64_t qq = in ? (int64_t)yy * P.W + xx : 0;
-      const float xc = in ? __ldg(logl + (int64_t)f * npix + qq) : 0.0f;
-      const float xp = !in ? 0.0f : (f == 0 ? last_l[qq] : __ldg(logl + (int64_t)(f - 1) * npix + qq));
-      xn[t] = xc - xp;
+    for (int j = 0; j < kT; ++j) {
+      const int f = P.f0 + s_first + j;
+#pragma unroll
+      for (int t = 0; t < 9; ++t) {
+        const int yy = py + t / 3 - 1, xx = px + t % 3 - 1;
+        const bool in = live && s_first + j < S && yy >= 0 && yy < P.H && xx >= 0 && xx < P.W;
+        const int64_t qq = in ? (int64_t)yy * P.W + xx : 0;
+        const float xc = in ? __ldg(logl + (int64_t)f * npix + qq) : 0.0f;
+        const float xp = !in ? 0.0f : (f == 0 ? last_l[qq] : __ldg(logl + (int64_t)(f - 1) * npix + qq));
+        xn[j][t] = xc - xp;
+      }
     }
   };
-  if (ks0 == 3) load_x9(0);
+  if (ks0 == 3 && stem_grp) load_x9(0);
   // TMA of the stem's input: the tile's row segment (tiles are whole row
   // segments when it is used), one box per chunk, two buffers
   const int tx0 = (int)(((int64_t)blockIdx.x * TP) % P.W), ty0 = (int)(((int64_t)blockIdx.x * TP) / P.W);
-  uint32_t tma_phase[2] = {0u, 0u};     // workers: parity of the next completion per buffer
+  uint32_t tma_phase[2] = {0u, 0u};     // stem group: parity of the next completion per buffer
   int tma_issued[2] = {0, 0};           // issuing thread: boxes issued per buffer
   auto issue_box = [&](int ch) {
     const int b = ch & 1;
@@ -275,11 +291,13 @@ evsnet_tct_kernel(const __grid_constant__ CUtensorMap tmap, TctParams P, const f
     tma_load_3d(xbuf + b * kBoxStride, &tmap, tx0 - 4, ty0 - 1, P.f0 + ch * kT - 1, &tma_bar[b]);
     ++tma_issued[b];
   };
-  // layer 0 on CUDA cores, FP32, of this thread's step of chunk ch into h0n:
-  // X_k = l_k - l_{k-1} (Eq. 1); the 3 x 3 stem reads its neighbours' X from
-  // xn (thread loads) or from the chunk's TMA box
-  float h0n[kHalf];
+  // layer 0 on CUDA cores, FP32, of chunk ch (stem group): X_k = l_k - l_{k-1}
+  // (Eq. 1); the 3 x 3 stem reads its neighbours' X from xn (thread loads) or
+  // from the chunk's TMA box.  The FP32 output goes to TMEM at once (the first
+  // residual block's input), the BF16-rounded one waits in h0p for layer 1's ring
+  uint32_t h0p[kT][CP / 2];
   auto stem = [&](int ch) {
+    float h0n[kT][CP];
     const int s0 = ch * kT, tc = min(kT, S - s0);
     if (P.tma && ch > 0) {
       const int b = ch & 1;
@@ -290,88 +308,95 @@ evsnet_tct_kernel(const __grid_constant__ CUtensorMap tmap, TctParams P, const f
       tma_phase[b] ^= 1u;
       const float* xb = xbuf + b * kBoxStride;
 #pragma unroll
-      for (int t = 0; t < 9; ++t) {
-        const int col = p + t % 3 + 3, row = t / 3;
-        xn[t] = xb[((1 + js) * 3 + row) * kBoxW + col] - xb[(js * 3 + row) * kBoxW + col];
-      }
-    }
-    if (ks0 == 0 && live) {
-      // the temporal layer 0's X ring: every thread of the pixel writes both
-      // steps (the same values), so that each reads back its own writes
-      for (int j = 0; j < tc; ++j) {
-        const int f = P.f0 + s0 + j;
-        const float xc = __ldg(logl + (int64_t)f * npix + q);
-        const float xp = f == 0 ? last_l[q] : __ldg(logl + (int64_t)(f - 1) * npix + q);
-        xh[ring_pos(s0 + j, R) * TP + p] = xc - xp;
-      }
-    }
-#pragma unroll
-    for (int c = 0; c < kHalf; ++c) h0n[c] = 0.0f;
-    if (js >= tc) return;
-    const int f = P.f0 + s0 + js;
-    float acc[kHalf];
-#pragma unroll
-    for (int c = 0; c < kHalf; ++c) acc[c] = bs[c0 + c];
-    if (live) {
-      if (ks0 == 3) {
+      for (int j = 0; j < kT; ++j)
 #pragma unroll
         for (int t = 0; t < 9; ++t) {
-          const float* wt = w0 + t * CP + c0;
-#pragma unroll
-          for (int c = 0; c < kHalf; ++c) acc[c] = fmaf(wt[c], xn[t], acc[c]);
+          const int col = p + t % 3 + 3, row = t / 3;
+          xn[j][t] = xb[((1 + j) * 3 + row) * kBoxW + col] - xb[(j * 3 + row) * kBoxW + col];
         }
-      } else if (ks0 > 0) {
-        const int r0 = ks0 >> 1;
-        for (int dy = 0; dy < ks0; ++dy) {
-          const int yy = py + dy - r0;
-          if (yy < 0 || yy >= P.H) continue;
-          for (int dx = 0; dx < ks0; ++dx) {
-            const int xx = px + dx - r0;
-            if (xx < 0 || xx >= P.W) continue;
-            const int64_t qq = (int64_t)yy * P.W + xx;
-            const float xc = __ldg(logl + (int64_t)f * npix + qq);
-            const float xp = f == 0 ? last_l[qq] : __ldg(logl + (int64_t)(f - 1) * npix + qq);
-            const float v = xc - xp;
-            const float* wt = w0 + (dy * ks0 + dx) * CP + c0;
-#pragma unroll
-            for (int c = 0; c < kHalf; ++c) acc[c] = fmaf(wt[c], v, acc[c]);
-          }
-        }
-      } else {
-        for (int tau0 = 0; tau0 < kt; ++tau0) {
-          const float v = xh[ring_pos(s0 + js - hk + tau0, R) * TP + p];
-          const float* wt = w0 + tau0 * CP + c0;
-#pragma unroll
-          for (int c = 0; c < kHalf; ++c) acc[c] = fmaf(wt[c], v, acc[c]);
-        }
-      }
     }
 #pragma unroll
-    for (int c = 0; c < kHalf; ++c) h0n[c] = live ? fmaxf(acc[c], 0.0f) : 0.0f;
+    for (int j = 0; j < kT; ++j) {
+#pragma unroll
+      for (int c = 0; c < CP; ++c) h0n[j][c] = 0.0f;
+      if (j >= tc) continue;
+      const int f = P.f0 + s0 + j;
+      float acc[CP];
+#pragma unroll
+      for (int c = 0; c < CP; ++c) acc[c] = bs[c];
+      if (live) {
+        if (ks0 == 3) {
+#pragma unroll
+          for (int t = 0; t < 9; ++t) {
+            const float* wt = w0 + t * CP;
+#pragma unroll
+            for (int c = 0; c < CP; ++c) acc[c] = fmaf(wt[c], xn[j][t], acc[c]);
+          }
+        } else if (ks0 > 0) {
+          const int r0 = ks0 >> 1;
+          for (int dy = 0; dy < ks0; ++dy) {
+            const int yy = py + dy - r0;
+            if (yy < 0 || yy >= P.H) continue;
+            for (int dx = 0; dx < ks0; ++dx) {
+              const int xx = px + dx - r0;
+              if (xx < 0 || xx >= P.W) continue;
+              const int64_t qq = (int64_t)yy * P.W + xx;
+              const float xc = __ldg(logl + (int64_t)f * npix + qq);
+              const float xp = f == 0 ? last_l[qq] : __ldg(logl + (int64_t)(f - 1) * npix + qq);
+              const float v = xc - xp;
+              const float* wt = w0 + (dy * ks0 + dx) * CP;
+#pragma unroll
+              for (int c = 0; c < CP; ++c) acc[c] = fmaf(wt[c], v, acc[c]);
+            }
+          }
+        } else {
+          const float xc = __ldg(logl + (int64_t)f * npix + q);
+          const float xp = f == 0 ? last_l[q] : __ldg(logl + (int64_t)(f - 1) * npix + q);
+          xh[ring_pos(s0 + j, R) * TP + p] = xc - xp;
+          for (int tau0 = 0; tau0 < kt; ++tau0) {
+            const float v = xh[ring_pos(s0 + j - hk + tau0, R) * TP + p];
+            const float* wt = w0 + tau0 * CP;
+#pragma unroll
+            for (int c = 0; c < CP; ++c) acc[c] = fmaf(wt[c], v, acc[c]);
+          }
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < CP; ++c) h0n[j][c] = live ? fmaxf(acc[c], 0.0f) : 0.0f;
+    }
+    if (residual && L >= 3) tmem_st32(hb_col(0, ch), &h0n[0][0]);
+#pragma unroll
+    for (int j = 0; j < kT; ++j)
+#pragma unroll
+      for (int c = 0; c < CP / 2; ++c) h0p[j][c] = pack_bf16(h0n[j][2 * c], h0n[j][2 * c + 1]);
   };
-  // this thread's step of chunk ch into layer 1's ring, and (residual form)
-  // the first block's FP32 input into TMEM for its closing layer
+  // chunk ch's BF16 layer-0 output into layer 1's ring
   auto stem_store = [&](int ch) {
-    const int s0 = ch * kT, tc = min(kT, S - s0);
-    if (js < tc) store_half(slot_of(1, ring_pos(s0 + js, R)), hc, p, h0n);
-    if (residual && L >= 3) tmem_st8(hb_col(0, ch & 1) + js * CP, h0n);
+    const int pc = ring_pos(ch * kT, R), tc = min(kT, S - ch * kT);
+#pragma unroll
+    for (int j = 0; j < kT; ++j) {
+      if (j >= tc) break;
+      unsigned char* slot = slot_of(1, pc + j >= R ? pc + j - R : pc + j);
+      *reinterpret_cast<uint4*>(slot + p * 16) = make_uint4(h0p[j][0], h0p[j][1], h0p[j][2], h0p[j][3]);
+      *reinterpret_cast<uint4*>(slot + kPlane + p * 16) = make_uint4(h0p[j][4], h0p[j][5], h0p[j][6], h0p[j][7]);
+    }
   };
   // chunk 0 before the first round (its previous frame may be the state's:
   // thread loads), chunk 1's box in flight
   if (tid == kIssuer && P.tma && nch > 1) issue_box(1);
-  if (worker && nch > 0) {
+  if (stem_grp && nch > 0) {
     stem(0);
     stem_store(0);
     if (ks0 == 3 && !P.tma) load_x9(kT);
   }
   // Rounds: in round tau tensor-core layer l computes chunk tau - l + 1 and
-  // layer 0 chunk tau + 1, so that one MMA issue, one barrier and one pass of
-  // epilogues serve every layer, and layer 0's CUDA-core work runs while the
-  // MMAs do.  Layer l's epilogue writes chunk tau - l + 1 into layer l + 1's
-  // ring, over the slots that layer l + 1's MMAs of the same round read: the
-  // MMAs are issued last layer first and each epilogue waits for its own
-  // layer's commit, which follows every later layer's MMAs; layer 0's output
-  // is stored after layer 1's epilogue, the round's last.
+  // layer 0 chunk tau + 1, so that one MMA issue and one barrier serve every
+  // layer, and layer 0's CUDA-core work runs while the MMAs do.  Layer l's
+  // epilogue writes chunk tau - l + 1 into layer l + 1's ring, over the slots
+  // that layer l + 1's MMAs of the same round read: the MMAs are issued last
+  // layer first and each epilogue waits for its own layer's commit, which
+  // follows every later layer's MMAs; layer 0's output is stored after layer
+  // 1's commit, the round's last.
   for (int tau = 0; tau < nch + L - 2; ++tau) {
     // ---- every tensor-core layer's MMAs, last layer first
     fence_proxy_async_smem();
@@ -419,12 +444,13 @@ evsnet_tct_kernel(const __grid_constant__ CUtensorMap tmap, TctParams P, const f
       }
     }
     // ---- layer 0 of the next chunk, in registers, while the MMAs run
-    if (worker && tau + 1 < nch) {
+    if (stem_grp && tau + 1 < nch) {
       stem(tau + 1);
       if (ks0 == 3 && !P.tma) load_x9((tau + 2) * kT);   // consumed next round
     }
-    // ---- epilogues, last layer first, each after its own layer's commit
+    // ---- this group's epilogues, last layer first, each after its layer's commit
     for (int l = L - 1; l >= 1 && worker; --l) {
+      if (!owns(l)) continue;
       const int c = tau - l + 1;
       if (c < 0 || c >= nch) continue;
       const int s0 = c * kT, tc = min(kT, S - s0), pc = ring_pos(s0, R);
@@ -436,65 +462,66 @@ evsnet_tct_kernel(const __grid_constant__ CUtensorMap tmap, TctParams P, const f
       lphase ^= 1u << l;
       tc_fence_after();
       const bool closing = residual && (l % 2) == 0;
-      // this thread's step and channel half of the accumulators (and of the
-      // block input for a closing layer)
-      float acc[kHalf], hin[kHalf];
-      if (closing) tmem_ld8x2(acc_col(l) + js * CP, hb_col(l / 2 - 1, c & 1) + js * CP, acc, hin);
-      else tmem_ld8(acc_col(l) + js * CP, acc);
-      float out[kHalf];
+      // both steps' accumulators (and the block input for a closing layer);
+      // acc then holds this layer's FP32 outputs
+      float acc[kT * CP], hin[kT * CP];
+      if (closing) tmem_ld32x2(acc_col(l), hb_col(l / 2 - 1, c), acc, hin);
+      else tmem_ld32(acc_col(l), acc);
+      float Is[kT];
 #pragma unroll
-      for (int c2 = 0; c2 < kHalf; ++c2) {
-        const float v = acc[c2] + bs[l * CP + c0 + c2];
-        const float o = closing ? fmaxf(hin[c2] + v, 0.0f) : fmaxf(v, 0.0f);
-        out[c2] = (live && js < tc) ? o : 0.0f;
-      }
-      if (l + 1 < L) {
-        if (js < tc) store_half(slot_of(l + 1, pc + js >= R ? pc + js - R : pc + js), hc, p, out);
-        // a closing layer's output is the next block's input
-        if (closing && l + 2 < L) tmem_st8(hb_col(l / 2, c & 1) + js * CP, out);
-      } else {
-        // ---- Eq. 6 projection and BiLIF, step by step: the partial sums of
-        // the pixel's other three threads reach thread group 0 through TMEM
-        // (the pixel's own lane, one column each)
-        float Ih = hc == 0 ? bp[0] : 0.0f;
+      for (int j = 0; j < kT; ++j) {
+        float* out = acc + j * CP;      // the outputs replace the accumulators
 #pragma unroll
-        for (int c2 = 0; c2 < kHalf; ++c2) Ih = fmaf(wp[c0 + c2], out[c2], Ih);
-        if (grp > 0) {
-          tmem_st1(tmem + lane_base + (uint32_t)(kPartCol + 8 * (grp - 1)), Ih);
-          tmem_wait_st();
+        for (int c2 = 0; c2 < CP; ++c2) {
+          const float v = out[c2] + bs[l * CP + c2];
+          const float o = closing ? fmaxf(hin[j * CP + c2] + v, 0.0f) : fmaxf(v, 0.0f);
+          out[c2] = (live && j < tc) ? o : 0.0f;
         }
-        tc_fence_before();
-        workers_sync();
-        tc_fence_after();
-        if (grp == 0) {
-          float p01, p10, p11;   // (step, half) = (0, 1), (1, 0), (1, 1)
-          tmem_ld1x3(tmem + lane_base + (uint32_t)kPartCol, tmem + lane_base + (uint32_t)(kPartCol + 8),
-                     tmem + lane_base + (uint32_t)(kPartCol + 16), p01, p10, p11);
-          const float Is[kT] = {Ih + p01, p10 + p11};
+        if (l + 1 < L) {
+          if (j < tc) store_row(slot_of(l + 1, pc + j >= R ? pc + j - R : pc + j), p, out);
+        } else {
+          // Eq. 6 projection
+          Is[j] = bp[0];
 #pragma unroll
-          for (int j = 0; j < kT; ++j) {
-            if (j >= tc) break;
-            const int f = P.f0 + s0 + j;
-            uint32_t nev = 0;
-            int Sp = 0;
-            if (live) {
-              const float I = Is[j];
-              const float vp = P.beta * V + I;
-              Sp = vp >= P.vth ? 1 : (vp <= -P.vth ? -1 : 0);
-              V = vp - P.reset * (float)Sp;
-              nev = (Sp != 0 && P.t0 + f >= 0) ? 1u : 0u;   // delayed labels below 0: none
-              const int64_t o = (int64_t)(s0 + j) * npix + q;
-              if (I_out) I_out[o] = I;
-              if (spikes) spikes[o] = (int8_t)Sp;
-            }
-            emit_events_warp(events, cap, n_events, nev, (uint32_t)px, (uint32_t)py, (uint32_t)(P.t0 + f), Sp);
+          for (int c2 = 0; c2 < CP; ++c2) Is[j] = fmaf(wp[c2], out[c2], Is[j]);
+        }
+      }
+      // a closing layer's output is the next block's input
+      if (closing && l + 2 < L) tmem_st32(hb_col(l / 2, c), acc);
+      if (l == L - 1) {
+        // BiLIF (Eq. 2-3) step by step and the events
+#pragma unroll
+        for (int j = 0; j < kT; ++j) {
+          if (j >= tc) break;
+          const int f = P.f0 + s0 + j;
+          uint32_t nev = 0;
+          int Sp = 0;
+          if (live) {
+            const float I = Is[j];
+            const float vp = P.beta * V + I;
+            Sp = vp >= P.vth ? 1 : (vp <= -P.vth ? -1 : 0);
+            V = vp - P.reset * (float)Sp;
+            nev = (Sp != 0 && P.t0 + f >= 0) ? 1u : 0u;   // delayed labels below 0: none
+            const int64_t o = (int64_t)(s0 + j) * npix + q;
+            if (I_out) I_out[o] = I;
+            if (spikes) spikes[o] = (int8_t)Sp;
           }
+          emit_events_warp(events, cap, n_events, nev, (uint32_t)px, (uint32_t)py, (uint32_t)(P.t0 + f), Sp);
         }
       }
     }
-    // layer 1's MMAs of this round are complete: chunk tau + 1 may overwrite
-    // the ring slots they read
-    if (worker && tau + 1 < nch) stem_store(tau + 1);
+    // layer 1's MMAs of this round are complete once its commit has arrived:
+    // chunk tau + 1 may then overwrite the ring slots they read
+    if (stem_grp && tau + 1 < nch) {
+      if (!owns(1)) {
+        if (!mbar_wait(&lbar[1], (lphase >> 1) & 1u, P.wait_iters)) {
+          if (lane == 0) atomicOr(n_events, kTimeoutBit);
+          bail = 1;
+        }
+        lphase ^= 2u;
+      }
+      stem_store(tau + 1);
+    }
     tmem_wait_st();
     tc_fence_before();
   }
@@ -510,15 +537,15 @@ evsnet_tct_kernel(const __grid_constant__ CUtensorMap tmap, TctParams P, const f
   } else if (live) {
     if (grp == 0) Vg[q] = V;
     // the last kt - 1 inputs of every layer back to the state, oldest first
-    // (the two step groups take alternate slots)
+    // (group g the slots j with j % 3 == g)
     for (int l = 1; l < L; ++l)
-      for (int j = js; j < hk; j += 2) {
-        float v[kHalf];
-        load_half(slot_of(l, ring_pos(S - hk + j, R)), hc, p, v);
-        for (int c = 0; c < kHalf; ++c)
-          if (c0 + c < C) hist[hidx(l, j, c0 + c)] = v[c];
+      for (int j = grp; j < hk; j += kGroups) {
+        float v[CP];
+        load_row(slot_of(l, ring_pos(S - hk + j, R)), p, v);
+        for (int c = 0; c < CP; ++c)
+          if (c < C) hist[hidx(l, j, c)] = v[c];
       }
-    if (ks0 == 0 && grp == 0)
+    if (ks0 == 0 && stem_grp)
       for (int j = 0; j < hk; ++j) hist[hidx(0, j, 0)] = xh[ring_pos(S - hk + j, R) * TP + p];
   }
   tc_fence_before();
