@@ -9,7 +9,7 @@
 // lane per pixel and three groups of 128 threads, one thread per pixel each
 // (warps w, w + 4, w + 8 share TMEM lane quarter w); group g runs the
 // epilogues of every third tensor-core layer counting down from the last, so
-// that consecutive layers' epilogues run at once in different warps; group 2
+// that consecutive layers' epilogues run at once in different warps; group 1
 // also runs layer 0, group 0 the projection and BiLIF.  A thirteenth warp's
 // one thread issues every MMA and TMA copy, so that issuing never holds up
 // the epilogues.  The input history of every layer >= 1 (its
@@ -74,7 +74,7 @@ constexpr int kSlot = TP * CP * 2;      // bytes of one ring slot
 constexpr int kPlane = TP * 16;         // bytes of 8 channels of 128 rows
 constexpr int kHalf = CP / 2;            // channels of one operand plane
 constexpr int kGroups = 3;              // worker groups, one thread per pixel each
-constexpr int kStemGroup = kGroups - 1; // the group that also runs layer 0
+constexpr int kStemGroup = 1;           // the group that also runs layer 0
 constexpr int kWorkers = kGroups * TP;
 constexpr int kThreads = kWorkers + 32; // and one warp that issues the MMAs and the TMA copies
 constexpr int kIssuer = kWorkers;       // its issuing thread
