@@ -5,7 +5,15 @@
 //   BF16 (kind::f16): weights and layer inputs rounded to BF16;
 //   FP8  (kind::f8f6f4, E4M3): weights scaled per output channel and layer
 //        inputs scaled per layer, tile and step, each by the power of two that
-//        brings its absolute maximum to at most 448 (E4M3's largest finite).
+//        brings a bound on its absolute maximum to at most 448 (E4M3's largest
+//        finite).  Weights: their maximum.  Layer inputs: layer 0's output is
+//        bounded by the tile's largest log difference times each channel's
+//        sum of |w0|; the output of tensor-core layer l by the largest value of
+//        its own input (taken while that input was written) times each output
+//        channel's sum of |w_l|, plus the bias -- no second pass over the
+//        accumulators.  E4M3 is a floating-point format, so a scale a few
+//        powers of two above the tight one costs precision only in values
+//        that fall below its normal range (2^-6 of the scale).
 //
 // Each CTA owns a 32 x 16 pixel tile for the whole call and walks the frames
 // in order; the membrane potentials of its pixels stay in shared memory.  For
@@ -109,6 +117,7 @@ evsnet_tc_kernel(TcParams P, const float* __restrict__ logl, const float* __rest
   __shared__ int bail;
   __shared__ unsigned int amax_bits;
   __shared__ float in_scale;            // FP8: scale of the current layer input
+  __shared__ float out_scale;           // FP8: scale of the current layer output (next input)
   constexpr int KS = ksteps<CP, kF8>();
   constexpr int EB = kF8 ? 1 : 2;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -127,6 +136,7 @@ evsnet_tc_kernel(TcParams P, const float* __restrict__ logl, const float* __rest
   float* bp = wp + CP;                    // [1] (+ padding)
   float* sw = bp + 4;                     // [L][CP] FP8 weight scales
   float* l0b = sw + L * CP;               // [CP] sum_t |w0[c][t]| (FP8 layer-0 bound)
+  float* gl = l0b + CP;                   // [L][CP] sum |w_l[c][.][.]| (FP8 bounds of layers 1..)
   float* cur = reinterpret_cast<float*>(sm + P.off_cur);
   float* prev = reinterpret_cast<float*>(sm + P.off_prev);
   float* Vs = reinterpret_cast<float*>(sm + P.off_V);
@@ -148,13 +158,18 @@ evsnet_tc_kernel(TcParams P, const float* __restrict__ logl, const float* __rest
   for (int i = tid; i < L * CP; i += kThreads) {
     const int l = i / CP, c = i % CP;
     bs[i] = c < C ? bg[l * C + c] : 0.0f;
-    float s = 1.0f;
+    float s = 1.0f, g = 0.0f;
     if (kF8 && l >= 1 && c < C) {
       float mx = 0.0f;
-      for (int k = 0; k < C * 9; ++k) mx = fmaxf(mx, fabsf(wg[9 * C + (l - 1) * C * C * 9 + c * C * 9 + k]));
+      for (int k = 0; k < C * 9; ++k) {
+        const float a = fabsf(wg[9 * C + (l - 1) * C * C * 9 + c * C * 9 + k]);
+        mx = fmaxf(mx, a);
+        g += a;
+      }
       s = e4m3_scale(mx);
     }
     sw[i] = s;
+    gl[i] = g;
   }
   const int wproj = 9 * C + (L - 1) * C * C * 9;
   for (int i = tid; i < CP; i += kThreads) wp[i] = i < C ? wg[wproj + i] : 0.0f;
@@ -219,9 +234,11 @@ evsnet_tc_kernel(TcParams P, const float* __restrict__ logl, const float* __rest
         float bound = 0.0f;
         for (int c = 0; c < C; ++c) bound = fmaxf(bound, fabsf(bs[c]) + xm * l0b[c]);
         in_scale = e4m3_scale(bound);
+        amax_bits = 0u;                 // next: the largest layer-0 output
       }
       __syncthreads();
     }
+    float amx0 = 0.0f;
     {
       const float inv = kF8 ? 1.0f / in_scale : 1.0f;
       for (int i = tid; i < (Hp - 2) * (Wp - 2); i += kThreads) {
@@ -250,11 +267,12 @@ evsnet_tc_kernel(TcParams P, const float* __restrict__ logl, const float* __rest
         }
         if (kF8) {
 #pragma unroll
-          for (int c = 0; c < CP; ++c) h[c] *= inv;
+          for (int c = 0; c < CP; ++c) { amx0 = fmaxf(amx0, h[c]); h[c] *= inv; }
         }
         store_row<CP, kF8>(act[0], P.plane, m, h);
       }
     }
+    if (kF8) atomicMax(&amax_bits, __float_as_uint(amx0));
     if (!kF8 && tid == 0) in_scale = 1.0f;
     // ---- tensor-core layers
     for (int l = 1; l < L; ++l) {
@@ -295,6 +313,14 @@ evsnet_tc_kernel(TcParams P, const float* __restrict__ logl, const float* __rest
           }
         }
         umma_commit(&mma_bar);
+        if (kF8 && l < L - 1) {
+          // the output's bound: h_c <= max(0, b_c + G_c max|input|), with a
+          // margin for the E4M3 roundings of weights and inputs
+          const float xm = 1.25f * __uint_as_float(amax_bits);
+          float bound = 0.0f;
+          for (int c = 0; c < C; ++c) bound = fmaxf(bound, fmaf(gl[l * CP + c], xm, bs[l * CP + c]));
+          out_scale = e4m3_scale(bound);
+        }
       }
       const bool ok = mbar_wait(&mma_bar, phase, P.wait_iters);
       phase ^= 1;
@@ -307,10 +333,8 @@ evsnet_tc_kernel(TcParams P, const float* __restrict__ logl, const float* __rest
       __syncthreads();
       if (bail) break;
       const bool last = l == L - 1;
-      // FP8 intermediate layers: a first pass over the accumulators finds the
-      // next layer's input scale
-      for (int pass = (kF8 && !last) ? 0 : 1; pass < 2; ++pass) {
-        const float inv_next = (kF8 && !last && pass == 1) ? 1.0f / in_scale : 1.0f;
+      {
+        const float inv_next = (kF8 && !last) ? 1.0f / out_scale : 1.0f;
         float amax = 0.0f;
         for (int b = warp >> 2; b < nb; b += 2) {
           const int m = m_start + b * 128 + (warp & 3) * 32 + lane;
@@ -329,13 +353,10 @@ evsnet_tc_kernel(TcParams P, const float* __restrict__ logl, const float* __rest
             h[c] = (need && inimg) ? fmaxf(fmaf(acc[c], deq, bs[l * CP + c]), 0.0f) : 0.0f;
           }
           if (!last) {
-            if (pass == 0) {
-#pragma unroll
-              for (int c = 0; c < CP; ++c) amax = fmaxf(amax, h[c]);
-            } else if (need) {
+            if (need) {
               if (kF8) {
 #pragma unroll
-                for (int c = 0; c < CP; ++c) h[c] *= inv_next;
+                for (int c = 0; c < CP; ++c) { amax = fmaxf(amax, h[c]); h[c] *= inv_next; }
               }
               store_row<CP, kF8>(aout, P.plane, m, h);
             }
@@ -358,11 +379,10 @@ evsnet_tc_kernel(TcParams P, const float* __restrict__ logl, const float* __rest
             emit_events_warp(events, cap, n_events, nev, (uint32_t)gx, (uint32_t)gy, (uint32_t)(P.t0 + f), S);
           }
         }
-        if (pass == 0) {
+        if (kF8 && !last) {
+          // the largest value of the next layer's input; its scale is this output's
           atomicMax(&amax_bits, __float_as_uint(amax));
-          __syncthreads();
-          if (tid == 0) in_scale = e4m3_scale(__uint_as_float(amax_bits));
-          __syncthreads();
+          if (tid == 0) in_scale = out_scale;
         }
       }
       tc_fence_before();
@@ -407,7 +427,7 @@ int launch(const float* logl, int32_t F, const et_evsnet_weights* net, et_evsnet
   P.off_act1 = 0;
   P.off_wB = al(P.act_bytes);
   P.off_f32 = P.off_wB + al(P.wB_bytes);
-  const int f32_bytes = 4 * (CP * 9 + P.L * CP + CP + 4 + P.L * CP + CP);
+  const int f32_bytes = 4 * (CP * 9 + P.L * CP + CP + 4 + P.L * CP + CP + P.L * CP);
   P.off_cur = P.off_f32 + al(f32_bytes);
   P.off_prev = P.off_cur + al(4 * P.Hp * P.Wp);
   P.off_V = P.off_prev + al(4 * P.Hp * P.Wp);

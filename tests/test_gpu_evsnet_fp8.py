@@ -1,8 +1,9 @@
 """Parity of the FP8 (E4M3) tensor-core EvSNet with the FP32 path and the oracle.
 
 The FP8 path rounds the weights of layers 1.. (scaled per output channel) and
-their inputs (scaled per layer, 32x16 tile and step) to E4M3 -- 4 significant
-bits, unit roundoff u = 2^-4 -- and accumulates in FP32.  Two kinds of check:
+their inputs (scaled per layer, 32x16 tile and step by a power of two from a
+bound on the input's maximum) to E4M3 -- 4 significant bits, unit roundoff
+u = 2^-4 -- and accumulates in FP32.  Two kinds of check:
 
 * exact: on data whose every weight and activation has at most 4 significant
   bits and a dynamic range inside E4M3's normal range, every rounding is exact
@@ -60,8 +61,10 @@ def _sparse_dyadic_net(seed, L, C):
     biases.  With log steps in {-2..2}/4 the first layer's outputs are k/8,
     k in {0, 1, 2}, and layer l's are k / 2^(3+l) with k <= 2^(l+1): for L <= 4
     every value has at most 4 significant bits, and every non-zero value is at
-    least 1/16 of the largest, so each E4M3 rounding after the power-of-two
-    scaling is exact."""
+    least 1/16 of the largest.  Each output channel's weights sum to at most 1
+    in magnitude, so the scale bound (1.25 x the input maximum) stays within
+    2.5x of the true maximum and every scaled value is a normal E4M3 number:
+    each rounding after the power-of-two scaling is exact."""
     assert L <= 4
     rng = np.random.default_rng(seed)
     d = inputs.random_evsnet(0, L, C, 1, 3, seed=seed, vth=0.05, beta=1.0)
