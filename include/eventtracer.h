@@ -286,9 +286,17 @@ int et_sensor_events(const float* logl, int32_t F, int32_t H, int32_t W,
  *   V' = beta V + I;  S = +1 if V' >= vth, -1 if V' <= -vth, else 0;  V = V' - reset S.
  * dtype: ET_F32 (CUDA cores), ET_BF16 or ET_FP8 (tensor cores, FP32 accumulation).
  *   ET_BF16 rounds the weights of layers 1.. and their inputs to BF16.
- *   ET_FP8 rounds them to E4M3 after scaling: weights per output channel and
- *   layer inputs per layer, 32x16 pixel tile and step, each by the power of two
- *   that brings its absolute maximum to at most 448 (exact to undo).
+ *   ET_FP8 rounds them to E4M3 after scaling by powers of two (exact to undo):
+ *   weights per output channel, by the one that brings their absolute maximum
+ *   to at most 448; layer inputs of the 3x3 form per layer, 32x16 pixel tile
+ *   and step, by the one that brings a bound on their maximum to at most 448
+ *   (the tile's largest log difference times the layer-0 weights' row sums for
+ *   layer 0's output, then the largest input times the layer's row sums plus
+ *   the bias); layer inputs of the pixel-wise form by the fixed per-layer
+ *   scales of `scales` (a tensor-core layer's MMA sums several time steps, so
+ *   their scales must agree): tensor-core layer l's input is divided by
+ *   scales[l - 1] and rounded to E4M3 with saturation at +-448
+ *   (et_evsnet_fp8_scales finds them on a calibration clip).
  *   Layer 0, the projection and BiLIF stay FP32 in both.
  * ks0 (this library's spatio-temporal form; the paper's EvSNet is pixel-wise):
  *   0, or an odd size 1..7 that makes layer 0 a one-step ks0 x ks0 spatial
@@ -308,6 +316,8 @@ typedef struct {
   int32_t delay;      /* event label offset (steps) */
   const float* w;     /* device */
   const float* b;     /* device */
+  const float* scales;  /* device float [n_layers - 1]: positive powers of two, the
+                           ET_FP8 pixel-wise form's input scales (NULL otherwise) */
 } et_evsnet_weights;
 
 /* Per-pixel state carried between calls (all device, caller-allocated):
@@ -330,12 +340,28 @@ typedef struct {
  *   I_out    device float [K][H][W] projection output (BiLIF input), or NULL
  *   spikes   device int8 [K][H][W] dense spikes, or NULL
  * K = F - 1 if the state was not initialized, else F.
- * Errors: ET_ERR_ARG, ET_ERR_UNIMPLEMENTED (C > 32, ks > 7, kt > 9, BF16 or FP8
- * for a shape the tensor-core kernel does not cover: it takes a plain stack of
- * 2 to 6 layers of 3x3 spatial convolutions), ET_ERR_CUDA. */
+ * Errors: ET_ERR_ARG (also: ET_FP8 for the pixel-wise form without scales),
+ * ET_ERR_UNIMPLEMENTED (C > 32, ks > 7, kt > 9, BF16 or FP8 for a shape the
+ * tensor-core kernels do not cover: plain stacks of 2 to 6 layers of 3x3
+ * spatial convolutions; the pixel-wise form with C <= 16, kt <= 7 and at least
+ * two layers), ET_ERR_CUDA. */
 int et_evsnet_forward(const float* logl, int32_t F, const et_evsnet_weights* net,
                       et_evsnet_state* state, int32_t t0, et_event* events, int64_t cap,
                       int64_t* n_events, float* I_out, int8_t* spikes, void* stream);
+
+/* Calibration of the FP8 pixel-wise form's input scales: runs the BF16
+ * tensor-core forward of `net` (its dtype and scales are ignored) over the F
+ * log frames (arguments and state as et_evsnet_forward; the state advances and
+ * no events are kept), takes the largest value m_l each tensor-core layer l
+ * receives, and writes scales[l - 1] = the smallest power of two s with
+ * headroom * m_l / s <= 448 (1 where m_l = 0).  scales: device float
+ * [n_layers - 1].  headroom >= 1 leaves room for inputs larger than the
+ * calibration clip's (beyond it they saturate).  Allocates and frees a few
+ * bytes of device memory (stream-ordered): not for the per-frame path.
+ * Errors: ET_ERR_ARG, ET_ERR_UNIMPLEMENTED (a shape the BF16 pixel-wise
+ * kernel does not cover), ET_ERR_CUDA. */
+int et_evsnet_fp8_scales(const float* logl, int32_t F, const et_evsnet_weights* net,
+                         et_evsnet_state* state, float headroom, float* scales, void* stream);
 
 /* ------------------------------------------------------------------ training
  * The learned form: EvSNet with FP32 weights, <= 16 channels, trained on B clips

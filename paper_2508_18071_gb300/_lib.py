@@ -42,7 +42,8 @@ class et_evsnet_weights(C.Structure):
     _fields_ = [("kind", C.c_int32), ("n_layers", C.c_int32), ("C", C.c_int32),
                 ("kt", C.c_int32), ("ks", C.c_int32), ("beta", C.c_float), ("vth", C.c_float),
                 ("reset", C.c_float), ("dtype", C.c_int32), ("ks0", C.c_int32),
-                ("delay", C.c_int32), ("w", C.c_void_p), ("b", C.c_void_p)]
+                ("delay", C.c_int32), ("w", C.c_void_p), ("b", C.c_void_p),
+                ("scales", C.c_void_p)]
 
 
 class et_evsnet_state(C.Structure):
@@ -72,6 +73,7 @@ SIGNATURES = {
     "et_render_profile_read": (i32, [P, P, P, P]),
     "et_threshold_events": (i32, [P, i32, i32, i32, f32, i32, P, i32, P, i64, P, P]),
     "et_evsnet_forward": (i32, [P, i32, P, P, i32, P, i64, P, P, P, P]),
+    "et_evsnet_fp8_scales": (i32, [P, i32, P, P, f32, P, P]),
     "et_train_workspace_bytes": (i32, [P, P, P]),
     "et_evsnet_train_forward": (i32, [P, P, P, P, P, P, P, P, P, C.c_size_t, P]),
     "et_emd_count_loss": (i32, [P, P, P, f32, P, P, P, P]),

@@ -363,6 +363,7 @@ class EvsNetDev:
     dtype: int = L.ET_F32
     ks0: int = 0
     delay: int = 0
+    scales: Optional[torch.Tensor] = None   # FP8 pixel-wise form: device [n_layers - 1]
 
     @staticmethod
     def from_dict(d: dict, dtype=L.ET_F32):
@@ -377,7 +378,8 @@ class EvsNetDev:
         b = self.b if b is None else b
         return L.et_evsnet_weights(self.kind, self.n_layers, self.C, self.kt, self.ks, self.beta,
                                    self.vth, self.reset, self.dtype, self.ks0, self.delay,
-                                   w.data_ptr(), b.data_ptr())
+                                   w.data_ptr(), b.data_ptr(),
+                                   self.scales.data_ptr() if self.scales is not None else None)
 
 
 class EvsStateDev:
@@ -416,6 +418,21 @@ class EvsStateDev:
         st.last_l.copy_(torch.as_tensor(z["last_l"]))
         st.initialized = int(z["initialized"])
         return st
+
+
+def evsnet_fp8_scales(logl: torch.Tensor, net: EvsNetDev, state: EvsStateDev, headroom=4.0,
+                      stream=None) -> torch.Tensor:
+    """et_evsnet_fp8_scales: the FP8 pixel-wise form's per-layer input scales
+    from a calibration clip (device float [n_layers - 1]); the state advances."""
+    F = logl.shape[0]
+    out = torch.empty(max(net.n_layers - 1, 1), dtype=torch.float32, device="cuda")
+    cw = net.c_struct()
+    cs = state.c_struct()
+    st = L.load().et_evsnet_fp8_scales(_ptr(logl), F, C.byref(cw), C.byref(cs), float(headroom),
+                                       _ptr(out), _stream(stream))
+    L.check("et_evsnet_fp8_scales", st)
+    state.initialized = cs.initialized
+    return out[:net.n_layers - 1]
 
 
 def evsnet_forward(logl: torch.Tensor, net: EvsNetDev, state: EvsStateDev, t0=0,

@@ -42,7 +42,7 @@ extern "C" int et_evsnet_forward(const float* logl, int32_t F, const et_evsnet_w
     if (rc == ET_ERR_UNIMPLEMENTED)
       rc = et_evsnet_forward_f32(logl, F, net, st, t0, events, cap, n_events, I_out, spikes, stream);
   }
-  else if (net->dtype == ET_BF16 && net->ks == 1)
+  else if ((net->dtype == ET_BF16 || net->dtype == ET_FP8) && net->ks == 1)
     rc = et_evsnet_forward_tct(logl, F, net, st, t0, events, cap, n_events, I_out, spikes, stream);
   else if ((net->dtype == ET_BF16 || net->dtype == ET_FP8) && net->ks0 == 0)
     rc = et_evsnet_forward_tc(logl, F, net, st, t0, events, cap, n_events, I_out, spikes, stream);

@@ -60,6 +60,7 @@
 #include "tc_ptx.cuh"
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <cstring>
 
 namespace {
@@ -70,7 +71,10 @@ constexpr int kT = 2;                   // steps per MMA round trip (the MMA sch
 static_assert(kT == 2, "one N = 32 MMA per middle slot covers exactly two steps");
 constexpr int kMaxKt = 7;
 constexpr int kMaxStem = 7;
-constexpr int kSlot = TP * CP * 2;      // bytes of one ring slot
+constexpr int kSlot = TP * CP * 2;      // bytes of one ring slot (BF16)
+constexpr int kSlot8 = TP * CP;         // bytes of one ring slot (FP8: 16 channels = one 16-byte row)
+constexpr int kPair8 = 2 * 2 * CP * 16; // bytes of one FP8 B block: K = 2 slots x N = 2 steps x 16 channels
+constexpr float kE4M3Max = 448.0f;
 constexpr int kPlane = TP * 16;         // bytes of 8 channels of 128 rows
 constexpr int kHalf = CP / 2;            // channels of one operand plane
 constexpr int kGroups = 3;              // worker groups, one thread per pixel each
@@ -95,6 +99,8 @@ struct TctParams {
   int off_wB, off_f32, off_xbuf;        // shared-memory byte offsets
   int tma;                              // the stem's input tiles come by TMA
   uint32_t wait_iters;
+  const float* scales;                  // FP8: input scale of tensor-core layer l at [l - 1]
+  unsigned int* amax;                   // calibration: largest input of layer l + 1 at [l] (float bits), or NULL
 };
 
 // the TMA box of the 3 x 3 stem: columns x0 - 4 .. x0 + 131, 3 rows, 3 frames
@@ -110,6 +116,27 @@ __device__ __forceinline__ int ring_pos(int s, int R) { return ((s % R) + R) % R
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
   return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+// smallest power of two >= x / 448 (1 for x == 0): the E4M3 scale of values
+// whose absolute maximum is x
+__host__ __device__ __forceinline__ float e4m3_scale(float x) {
+  if (!(x > 0.0f)) return 1.0f;
+  int e;
+  const float m = frexpf(x / kE4M3Max, &e);   // x / 448 = m 2^e, m in [0.5, 1)
+  return ldexpf(1.0f, m == 0.5f ? e - 1 : e);
+}
+
+// four floats as four E4M3 bytes (saturating), the first in the low byte
+__device__ __forceinline__ uint32_t pack_e4m3(float a, float b, float c, float d) {
+  const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
+  const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(c, d), __NV_SATFINITE, __NV_E4M3);
+  return lo | (hi << 16);
+}
+
+__device__ __forceinline__ float2 unpack_e4m3x2(uint32_t two) {
+  const __half2_raw h = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)two, __NV_E4M3);
+  return __half22float2(*reinterpret_cast<const __half2*>(&h));
 }
 
 __device__ __forceinline__ float2 unpack_bf16(uint32_t w) {
@@ -149,6 +176,36 @@ __device__ __forceinline__ void load_row(const unsigned char* slot, int m, float
   }
 }
 
+// FP8: the 16 channels of one pixel divided by the layer's input scale (inv =
+// its reciprocal), as row m of a ring slot and of the slot's copy R positions
+// on, if it has one (the ring is kept twice so that every window of slots is
+// contiguous)
+__device__ __forceinline__ void store_row8(unsigned char* slot, unsigned char* copy, int m, const float* v,
+                                           float inv) {
+  uint4 r;
+  r.x = pack_e4m3(v[0] * inv, v[1] * inv, v[2] * inv, v[3] * inv);
+  r.y = pack_e4m3(v[4] * inv, v[5] * inv, v[6] * inv, v[7] * inv);
+  r.z = pack_e4m3(v[8] * inv, v[9] * inv, v[10] * inv, v[11] * inv);
+  r.w = pack_e4m3(v[12] * inv, v[13] * inv, v[14] * inv, v[15] * inv);
+  *reinterpret_cast<uint4*>(slot + m * 16) = r;
+  if (copy) *reinterpret_cast<uint4*>(copy + m * 16) = r;
+}
+
+// and back, times the scale
+__device__ __forceinline__ void load_row8(const unsigned char* slot, int m, float sc, float (&v)[CP]) {
+  const uint4 a = *reinterpret_cast<const uint4*>(slot + m * 16);
+  const uint32_t w[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float2 f0 = unpack_e4m3x2(w[i] & 0xFFFFu), f1 = unpack_e4m3x2(w[i] >> 16);
+    v[4 * i] = f0.x * sc;
+    v[4 * i + 1] = f0.y * sc;
+    v[4 * i + 2] = f1.x * sc;
+    v[4 * i + 3] = f1.y * sc;
+  }
+}
+
+template <bool kF8, bool kCal>
 __global__ void __launch_bounds__(kThreads, 1)
 evsnet_tct_kernel(const __grid_constant__ CUtensorMap tmap, TctParams P, const float* __restrict__ logl,
                   const float* __restrict__ wg, const float* __restrict__ bg, float* __restrict__ Vg,
@@ -175,8 +232,13 @@ evsnet_tct_kernel(const __grid_constant__ CUtensorMap tmap, TctParams P, const f
   const bool stem_grp = grp == kStemGroup;
   const bool live = worker && q < npix;
   const int px = live ? (int)(q % P.W) : 0, py = live ? (int)(q / P.W) : 0;
-  unsigned char* rings = sm;                                   // [L-1][R] slots
-  unsigned char* wB = sm + P.off_wB;                           // [L-1][kt] 16 x 16 BF16
+  constexpr int kSB = kF8 ? kSlot8 : kSlot;                    // bytes per ring slot
+  // slots per layer.  FP8: positions R .. RS - 1 repeat 0 .. RS - R - 1; a
+  // window starts below R and its slot pairs end at kt + 1 (kt odd) or kt + 2
+  // (kt even) slots, so the copy of position R - 1 is needed for even kt only
+  const int RS = kF8 ? ((kt & 1) ? 2 * R - 1 : 2 * R) : R;
+  unsigned char* rings = sm;                                   // [L-1][RS] slots
+  unsigned char* wB = sm + P.off_wB;                           // BF16: [L-1][kt] 16 x 16; FP8: [L-1][pairs] kPair8
   float* f32 = reinterpret_cast<float*>(sm + P.off_f32);
   float* bs = f32;                                             // [L][CP] biases
   float* wp = bs + L * CP;                                     // [CP] projection
@@ -184,8 +246,17 @@ evsnet_tct_kernel(const __grid_constant__ CUtensorMap tmap, TctParams P, const f
   float* w0 = bp + 4;                                          // [taps][CP] layer 0
   const int taps0 = ks0 > 0 ? ks0 * ks0 : kt;
   float* xh = w0 + taps0 * CP;                                 // [R][TP] layer-0 X ring (temporal layer 0)
+  float* dq = xh + (ks0 == 0 ? R * TP : 0);                    // FP8: [L][CP] weight scale, then x input scale
+  float* isc = dq + L * CP;                                    // FP8: [kMaxLayers] 1 / input scale of layer l
+  float* scl = isc + kMaxLayers;                               // FP8: [kMaxLayers] input scale of layer l
+  const int npairs = (kt + 2) / 2;                             // FP8: MMAs per layer (slot pairs)
   float* xbuf = reinterpret_cast<float*>(sm + P.off_xbuf);     // [2][3 frames][3 rows][kBoxW] (TMA)
-  auto slot_of = [&](int l, int pos) { return rings + ((size_t)(l - 1) * R + pos) * kSlot; };
+  auto slot_of = [&](int l, int pos) { return rings + ((size_t)(l - 1) * RS + pos) * kSB; };
+  // a pixel's 16 channels into ring position pos of layer l (both copies in FP8)
+  auto put_row = [&](int l, int pos, const float* v) {
+    if constexpr (kF8) store_row8(slot_of(l, pos), pos + R < RS ? slot_of(l, pos + R) : nullptr, p, v, isc[l]);
+    else store_row(slot_of(l, pos), p, v);
+  };
   // history element (layer l, oldest-first slot j, channel c) of this pixel in the state
   auto hidx = [&](int l, int j, int c) -> int64_t { return (((int64_t)l * hk + j) * C + c) * npix + q; };
 
@@ -200,16 +271,73 @@ evsnet_tct_kernel(const __grid_constant__ CUtensorMap tmap, TctParams P, const f
     const int t = i / CP, c = i % CP;
     w0[i] = c < C ? wg[c * taps0 + t] : 0.0f;                 // layer 0: [C][1][taps]
   }
-  // B operands: one strip per layer l >= 1 of kt blocks of 16 rows, block b
-  // holding tap kt - 1 - b (rows n = output channel, K = input channel in two
-  // planes of 8, each plane kt x 16 rows of 16 bytes)
-  for (int i = tid; i < (L - 1) * kt * CP * CP; i += kThreads) {
-    const int k = i % CP, n = (i / CP) % CP, tau = (i / (CP * CP)) % kt, l = 1 + i / (CP * CP * kt);
-    float v = 0.0f;
-    if (n < C && k < C) v = wg[P.woff[l] + (n * C + k) * kt + tau];
-    unsigned char* dst = wB + (size_t)(l - 1) * kt * (CP * CP * 2) + (k >> 3) * (kt * CP * 16) +
-                         ((kt - 1 - tau) * CP + n) * 16 + (k & 7) * 2;
-    *reinterpret_cast<__nv_bfloat16*>(dst) = __float2bfloat16_rn(v);
+  if constexpr (!kF8) {
+    // B operands: one strip per layer l >= 1 of kt blocks of 16 rows, block b
+    // holding tap kt - 1 - b (rows n = output channel, K = input channel in two
+    // planes of 8, each plane kt x 16 rows of 16 bytes)
+    // (one 16-byte row of 8 input channels per iteration: its loads in flight together)
+    for (int r = tid; r < (L - 1) * 2 * kt * CP; r += kThreads) {
+      const int n = r % CP, b = (r / CP) % kt, pl = (r / (CP * kt)) % 2, l = 1 + r / (2 * CP * kt);
+      const int tau = kt - 1 - b;
+      float v[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int k = pl * 8 + e;
+        v[e] = (n < C && k < C) ? __ldg(wg + P.woff[l] + (n * C + k) * kt + tau) : 0.0f;
+      }
+      *reinterpret_cast<uint4*>(wB + (size_t)(l - 1) * kt * (CP * CP * 2) + pl * (kt * CP * 16) + (b * CP + n) * 16) =
+          make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
+    }
+  } else {
+    // the FP32 weights of layers 1.. staged in the ring area (free until the
+    // ring is zeroed below), read once with coalesced loads
+    float* wst = reinterpret_cast<float*>(rings);
+    const int wbase = P.woff[1], nw = P.woff[L] - P.woff[1];
+#pragma unroll 4
+    for (int i = tid; i < nw; i += kThreads) wst[i] = __ldg(wg + wbase + i);
+    for (int l = tid; l < kMaxLayers; l += kThreads) {
+      const float sc = (l >= 1 && l < L) ? P.scales[l - 1] : 1.0f;
+      scl[l] = sc;
+      isc[l] = 1.0f / sc;
+    }
+    __syncthreads();
+    // weight scales per layer and output channel (their maximum to <= 448)
+    for (int i = tid; i < L * CP; i += kThreads) {
+      const int l = i / CP, co = i % CP;
+      float mx = 0.0f;
+      if (l >= 1 && co < C)
+        for (int k = 0; k < C * kt; ++k) mx = fmaxf(mx, fabsf(wst[P.woff[l] - wbase + co * C * kt + k]));
+      dq[i] = e4m3_scale(mx);
+    }
+    __syncthreads();
+    // B operands: per layer l >= 1 one block per pair of slots (2 pi, 2 pi + 1)
+    // of the window: K = the two slots' 16 channels (two 16-byte columns of 32
+    // rows), N = 32 = (step j, output channel); slot i feeds step j through tap
+    // i - j (zero outside 0 .. kt - 1)
+    // (one 16-byte row of 16 input channels per iteration; the weight scales
+    // are powers of two, so multiplying by their reciprocals is exact)
+    for (int row = tid; row < (L - 1) * npairs * 2 * 2 * CP; row += kThreads) {
+      const int n = row % (2 * CP), r = (row / (2 * CP)) % 2, pi = (row / (4 * CP)) % npairs;
+      const int l = 1 + row / (4 * CP * npairs);
+      const int j = n / CP, co = n % CP, tau = 2 * pi + r - j;
+      const bool on = tau >= 0 && tau < kt && co < C;
+      const float inv = 1.0f / dq[l * CP + co];
+      float v[CP];
+#pragma unroll
+      for (int ci = 0; ci < CP; ++ci)
+        v[ci] = (on && ci < C) ? wst[P.woff[l] - wbase + (co * C + ci) * kt + tau] * inv : 0.0f;
+      *reinterpret_cast<uint4*>(wB + ((size_t)(l - 1) * npairs + pi) * kPair8 + r * (2 * CP * 16) + n * 16) =
+          make_uint4(pack_e4m3(v[0], v[1], v[2], v[3]), pack_e4m3(v[4], v[5], v[6], v[7]),
+                     pack_e4m3(v[8], v[9], v[10], v[11]), pack_e4m3(v[12], v[13], v[14], v[15]));
+    }
+    __syncthreads();
+    // dequantisation factor of layer l's accumulators: weight scale x input
+    // scale; the rings zeroed: a slot pair may take one slot the call never
+    // writes (with zero weights), whose bytes must not be E4M3 NaNs
+    for (int i = tid; i < L * CP; i += kThreads) dq[i] *= scl[i / CP];
+    for (int i = tid; i < (L - 1) * RS * kSlot8 / 16; i += kThreads)
+      reinterpret_cast<uint4*>(rings)[i] = make_uint4(0u, 0u, 0u, 0u);
+    __syncthreads();
   }
   // ring slots of steps -(kt-1) .. -1 from the state (oldest first): group g
   // fills the slots j with j % 3 == g (both channel halves), a layer's loads
@@ -226,9 +354,7 @@ evsnet_tct_kernel(const __grid_constant__ CUtensorMap tmap, TctParams P, const f
 #pragma unroll
     for (int jj = 0; jj < kJ; ++jj) {
       const int j = jj * kGroups + grp;
-      if (worker && j < hk) {
-        store_row(slot_of(l, ring_pos(j - hk, R)), p, v[jj]);
-      }
+      if (worker && j < hk) put_row(l, ring_pos(j - hk, R), v[jj]);
     }
   }
   if (ks0 == 0 && stem_grp)
@@ -248,8 +374,12 @@ evsnet_tct_kernel(const __grid_constant__ CUtensorMap tmap, TctParams P, const f
   const uint32_t tmem = tmem_slot;
   const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
   const uint32_t idesc16 = umma_idesc_bf16(TP, CP), idesc32 = umma_idesc_bf16(TP, 2 * CP);
-  const uint64_t a_desc0 = umma_desc(smem_u32(rings), kPlane, 128);
-  const uint64_t b_desc0 = umma_desc(smem_u32(wB), kt * CP * 16, 128);
+  const uint32_t idesc8 = umma_idesc_e4m3(TP, 2 * CP);
+  // A: K-adjacent 16-byte columns are the two channel planes of a BF16 slot,
+  // or two consecutive FP8 slots; B: the two planes of a BF16 tap strip, or the
+  // two slot columns of an FP8 pair block
+  const uint64_t a_desc0 = umma_desc(smem_u32(rings), kF8 ? kSlot8 : kPlane, 128);
+  const uint64_t b_desc0 = umma_desc(smem_u32(wB), kF8 ? 2 * CP * 16 : kt * CP * 16, 128);
   // TMEM columns: layer l's accumulators (both steps, 16 channels each) at
   // 32 (l - 1); the FP32 block inputs of the residual form (block b, chunk c)
   // at kHbCol + 32 (3 b + c % 3): a block input written for chunk c + 2 never
@@ -295,7 +425,7 @@ evsnet_tct_kernel(const __grid_constant__ CUtensorMap tmap, TctParams P, const f
   // (Eq. 1); the 3 x 3 stem reads its neighbours' X from xn (thread loads) or
   // from the chunk's TMA box.  The FP32 output goes to TMEM at once (the first
   // residual block's input), the BF16-rounded one waits in h0p for layer 1's ring
-  uint32_t h0p[kT][CP / 2];
+  uint32_t h0p[kT][kF8 ? CP / 4 : CP / 2];
   auto stem = [&](int ch) {
     float h0n[kT][CP];
     const int s0 = ch * kT, tc = min(kT, S - s0);
@@ -365,10 +495,28 @@ evsnet_tct_kernel(const __grid_constant__ CUtensorMap tmap, TctParams P, const f
       for (int c = 0; c < CP; ++c) h0n[j][c] = live ? fmaxf(acc[c], 0.0f) : 0.0f;
     }
     if (residual && L >= 3) tmem_st32(hb_col(0, ch), &h0n[0][0]);
+    if (kCal) {
+      float m = 0.0f;
 #pragma unroll
-    for (int j = 0; j < kT; ++j)
+      for (int j = 0; j < kT; ++j)
 #pragma unroll
-      for (int c = 0; c < CP / 2; ++c) h0p[j][c] = pack_bf16(h0n[j][2 * c], h0n[j][2 * c + 1]);
+        for (int c = 0; c < CP; ++c) m = fmaxf(m, h0n[j][c]);
+      const unsigned r = __reduce_max_sync(0xFFFFFFFFu, __float_as_uint(m));
+      if (lane == 0) atomicMax(P.amax, r);
+    }
+#pragma unroll
+    for (int j = 0; j < kT; ++j) {
+      if constexpr (kF8) {
+        const float inv = isc[1];
+#pragma unroll
+        for (int c = 0; c < CP / 4; ++c)
+          h0p[j][c] = pack_e4m3(h0n[j][4 * c] * inv, h0n[j][4 * c + 1] * inv, h0n[j][4 * c + 2] * inv,
+                                h0n[j][4 * c + 3] * inv);
+      } else {
+#pragma unroll
+        for (int c = 0; c < CP / 2; ++c) h0p[j][c] = pack_bf16(h0n[j][2 * c], h0n[j][2 * c + 1]);
+      }
+    }
   };
   // chunk ch's BF16 layer-0 output into layer 1's ring
   auto stem_store = [&](int ch) {
@@ -376,9 +524,16 @@ evsnet_tct_kernel(const __grid_constant__ CUtensorMap tmap, TctParams P, const f
 #pragma unroll
     for (int j = 0; j < kT; ++j) {
       if (j >= tc) break;
-      unsigned char* slot = slot_of(1, pc + j >= R ? pc + j - R : pc + j);
+      const int pos = pc + j >= R ? pc + j - R : pc + j;
+      unsigned char* slot = slot_of(1, pos);
       *reinterpret_cast<uint4*>(slot + p * 16) = make_uint4(h0p[j][0], h0p[j][1], h0p[j][2], h0p[j][3]);
-      *reinterpret_cast<uint4*>(slot + kPlane + p * 16) = make_uint4(h0p[j][4], h0p[j][5], h0p[j][6], h0p[j][7]);
+      if constexpr (kF8) {
+        if (pos + R < RS)
+          *reinterpret_cast<uint4*>(slot_of(1, pos + R) + p * 16) = make_uint4(h0p[j][0], h0p[j][1], h0p[j][2], h0p[j][3]);
+      }
+      else
+        *reinterpret_cast<uint4*>(slot + kPlane + p * 16) =
+            make_uint4(h0p[j][4], h0p[j][5], h0p[j][6], h0p[j][7]);
     }
   };
   // chunk 0 before the first round (its previous frame may be the state's:
@@ -419,11 +574,25 @@ evsnet_tct_kernel(const __grid_constant__ CUtensorMap tmap, TctParams P, const f
         const int c = tau - l + 1;
         if (c < 0 || c >= nch) continue;
         const int tc = min(kT, S - c * kT);
+        const uint32_t d = tmem + (uint32_t)((l - 1) * kT * CP);
+        if constexpr (kF8) {
+          // slot pairs (2 pi, 2 pi + 1) of the window, both steps at once; the
+          // doubled ring keeps the window's slots p0 .. p0 + kt + 1 contiguous
+          const uint64_t a0 = a_desc0 + (uint64_t)((l - 1) * RS + p0) * (kSlot8 >> 4);
+          const uint64_t b0 = b_desc0 + (uint64_t)((l - 1) * npairs) * (kPair8 >> 4);
+#pragma unroll
+          for (int pi = 0; pi < (kMaxKt + 2) / 2; ++pi) {
+            if (pi >= npairs) break;
+            umma_e4m3(d, a0 + (uint64_t)(2 * pi) * (kSlot8 >> 4), b0 + (uint64_t)pi * (kPair8 >> 4), idesc8,
+                      pi != 0);
+          }
+          umma_commit(&lbar[l]);
+          continue;
+        }
         // descriptors differ only in their start-address field (16-byte units):
         // slots are 4 KB apart, B blocks 256 B
         const uint64_t a0 = a_desc0 + (uint64_t)((l - 1) * R) * kSlotU;
         const uint64_t b0 = b_desc0 + (uint64_t)((l - 1) * kt) * ((CP * CP * 2) >> 4);
-        const uint32_t d = tmem + (uint32_t)((l - 1) * kT * CP);
         // slot 0 starts step 0 (tap 0), slot kt starts step 1 (tap kt - 1);
         // slots 1 .. kt - 1 add to both (taps i and i - 1)
         uint64_t bw = b0 + (uint64_t)(kt - 1) * kBlock;
@@ -473,12 +642,13 @@ evsnet_tct_kernel(const __grid_constant__ CUtensorMap tmap, TctParams P, const f
         float* out = acc + j * CP;      // the outputs replace the accumulators
 #pragma unroll
         for (int c2 = 0; c2 < CP; ++c2) {
-          const float v = out[c2] + bs[l * CP + c2];
+          // FP8: the accumulators carry the weight and input scales
+          const float v = kF8 ? fmaf(out[c2], dq[l * CP + c2], bs[l * CP + c2]) : out[c2] + bs[l * CP + c2];
           const float o = closing ? fmaxf(hin[j * CP + c2] + v, 0.0f) : fmaxf(v, 0.0f);
           out[c2] = (live && j < tc) ? o : 0.0f;
         }
         if (l + 1 < L) {
-          if (j < tc) store_row(slot_of(l + 1, pc + j >= R ? pc + j - R : pc + j), p, out);
+          if (j < tc) put_row(l + 1, pc + j >= R ? pc + j - R : pc + j, out);
         } else {
           // Eq. 6 projection
           Is[j] = bp[0];
@@ -488,6 +658,14 @@ evsnet_tct_kernel(const __grid_constant__ CUtensorMap tmap, TctParams P, const f
       }
       // a closing layer's output is the next block's input
       if (closing && l + 2 < L) tmem_st32(hb_col(l / 2, c), acc);
+      if (kCal && l + 1 < L) {
+        // calibration: the largest input of layer l + 1 (outputs are >= 0)
+        float m = 0.0f;
+#pragma unroll
+        for (int i = 0; i < kT * CP; ++i) m = fmaxf(m, acc[i]);
+        const unsigned r = __reduce_max_sync(0xFFFFFFFFu, __float_as_uint(m));
+        if (lane == 0) atomicMax(P.amax + l, r);
+      }
       if (l == L - 1) {
         // BiLIF (Eq. 2-3) step by step and the events
 #pragma unroll
@@ -541,7 +719,8 @@ evsnet_tct_kernel(const __grid_constant__ CUtensorMap tmap, TctParams P, const f
     for (int l = 1; l < L; ++l)
       for (int j = grp; j < hk; j += kGroups) {
         float v[CP];
-        load_row(slot_of(l, ring_pos(S - hk + j, R)), p, v);
+        if constexpr (kF8) load_row8(slot_of(l, ring_pos(S - hk + j, R)), p, scl[l], v);
+        else load_row(slot_of(l, ring_pos(S - hk + j, R)), p, v);
         for (int c = 0; c < CP; ++c)
           if (c < C) hist[hidx(l, j, c)] = v[c];
       }
@@ -556,15 +735,19 @@ evsnet_tct_kernel(const __grid_constant__ CUtensorMap tmap, TctParams P, const f
 
 }  // namespace
 
-// BF16 tensor-core path of the pixel-wise form; declines (before launching
-// anything) what it does not cover.
-int et_evsnet_forward_tct(const float* logl, int32_t F, const et_evsnet_weights* net,
-                          et_evsnet_state* st, int32_t t0, et_event* events, int64_t cap,
-                          int64_t* n_events, float* I_out, int8_t* spikes, cudaStream_t stream) {
-  if (net->dtype != ET_BF16 || net->ks != 1 || net->C > CP || net->kt > kMaxKt || net->ks0 > kMaxStem ||
-      net->n_layers < 2)
+namespace {
+
+// the pixel-wise form on the tensor cores with BF16 (f8 false) or FP8 operands;
+// amax (calibration, BF16 only): device [n_layers - 1] float bits, maxima added
+int tct_launch(const float* logl, int32_t F, const et_evsnet_weights* net, et_evsnet_state* st, int32_t t0,
+               et_event* events, int64_t cap, int64_t* n_events, float* I_out, int8_t* spikes, bool f8,
+               unsigned int* amax, cudaStream_t stream) {
+  if (net->ks != 1 || net->C > CP || net->kt > kMaxKt || net->ks0 > kMaxStem || net->n_layers < 2)
     return ET_ERR_UNIMPLEMENTED;
+  if (f8 && !net->scales) return ET_ERR_ARG;
   TctParams P{};
+  P.scales = net->scales;
+  P.amax = amax;
   P.H = st->H; P.W = st->W; P.F = F; P.f0 = st->initialized ? 0 : 1; P.t0 = t0;
   P.L = net->n_layers; P.C = net->C; P.kt = net->kt; P.ks0 = net->ks0; P.kind = net->kind;
   P.beta = net->beta; P.vth = net->vth; P.reset = net->reset;
@@ -576,12 +759,15 @@ int et_evsnet_forward_tct(const float* logl, int32_t F, const et_evsnet_weights*
   }
   P.woff[P.L] = wo;
   P.wait_iters = et_tc_wait_iters();
-  const size_t rings = (size_t)(P.L - 1) * P.R * kSlot;
-  const size_t wbytes = (size_t)(P.L - 1) * P.kt * CP * CP * 2;
+  // FP8: the rings twice over in half-size slots, one B block per slot pair
+  const size_t rings = (size_t)(P.L - 1) * (f8 ? (size_t)((P.kt & 1) ? 2 * P.R - 1 : 2 * P.R) * kSlot8
+                                                 : (size_t)P.R * kSlot);
+  const size_t wbytes = (size_t)(P.L - 1) * (f8 ? (size_t)((P.kt + 2) / 2) * kPair8 : (size_t)P.kt * CP * CP * 2);
   const int taps0 = P.ks0 > 0 ? P.ks0 * P.ks0 : P.kt;
   // the X ring of a temporal layer 0 (not kept with a stem)
   const size_t fbytes = sizeof(float) * ((size_t)P.L * CP + CP + 4 + (size_t)taps0 * CP +
-                                         (P.ks0 == 0 ? (size_t)P.R * TP : 0));
+                                         (P.ks0 == 0 ? (size_t)P.R * TP : 0) +
+                                         (f8 ? (size_t)P.L * CP + 2 * kMaxLayers : 0));
   P.off_wB = (int)rings;
   P.off_f32 = (int)(rings + wbytes);
   // TMA of the 3 x 3 stem's input: tiles must be row segments and the frames'
@@ -617,15 +803,81 @@ int et_evsnet_forward_tct(const float* logl, int32_t F, const et_evsnet_weights*
   ET_CHECK_CUDA(cudaGetDevice(&dev));
   ET_CHECK_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   // static shared memory (barriers, TMEM slot, flag) comes on top of the dynamic part
+  auto kern = f8 ? evsnet_tct_kernel<true, false>
+                 : (amax ? evsnet_tct_kernel<false, true> : evsnet_tct_kernel<false, false>);
   cudaFuncAttributes fa;
-  ET_CHECK_CUDA(cudaFuncGetAttributes(&fa, evsnet_tct_kernel));
+  ET_CHECK_CUDA(cudaFuncGetAttributes(&fa, kern));
   if (smem + fa.sharedSizeBytes > (size_t)max_smem) return ET_ERR_UNIMPLEMENTED;
   if (P.kt > 1 && !st->hist) return ET_ERR_ARG;
-  ET_CHECK_CUDA(cudaFuncSetAttribute(evsnet_tct_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  ET_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int64_t npix = (int64_t)P.H * P.W;
-  evsnet_tct_kernel<<<(unsigned)((npix + TP - 1) / TP), kThreads, smem, stream>>>(
+  kern<<<(unsigned)((npix + TP - 1) / TP), kThreads, smem, stream>>>(
       tmap, P, logl, net->w, net->b, st->V, st->hist, st->last_l, events, cap,
       reinterpret_cast<unsigned long long*>(n_events), I_out, spikes);
   ET_CHECK_LAUNCH();
   return ET_OK;
+}
+
+// the largest layer inputs -> power-of-two scales with headroom (NaN where a
+// bounded wait of the calibration run gave up)
+__global__ void fp8_scales_kernel(const unsigned int* amax, const int64_t* n_ev, int n, float headroom,
+                                  float* scales) {
+  const int i = threadIdx.x;
+  const bool timed_out = ((unsigned long long)*n_ev & kTimeoutBit) != 0;
+  if (i < n) scales[i] = timed_out ? __int_as_float(0x7FC00000) : e4m3_scale(headroom * __uint_as_float(amax[i]));
+}
+
+}  // namespace
+
+// Tensor-core path of the pixel-wise form (BF16, or FP8 with the net's input
+// scales); declines (before launching anything) what it does not cover.
+int et_evsnet_forward_tct(const float* logl, int32_t F, const et_evsnet_weights* net,
+                          et_evsnet_state* st, int32_t t0, et_event* events, int64_t cap,
+                          int64_t* n_events, float* I_out, int8_t* spikes, cudaStream_t stream) {
+  if (net->dtype != ET_BF16 && net->dtype != ET_FP8) return ET_ERR_UNIMPLEMENTED;
+  return tct_launch(logl, F, net, st, t0, events, cap, n_events, I_out, spikes, net->dtype == ET_FP8, nullptr,
+                    stream);
+}
+
+extern "C" int et_evsnet_fp8_scales(const float* logl, int32_t F, const et_evsnet_weights* net,
+                                    et_evsnet_state* st, float headroom, float* scales, void* stream_) {
+  if (!net || !st || !scales || F < 1 || !logl || !net->w || !net->b || !st->V || !st->last_l) return ET_ERR_ARG;
+  if (!(headroom >= 1.0f) || !(headroom <= 1e30f)) return ET_ERR_ARG;
+  if (net->n_layers < 2 || net->n_layers > kMaxLayers || net->C < 1 || net->kt < 1 || net->ks != 1 ||
+      net->ks0 < 0 || net->ks0 > 7 || (net->ks0 > 0 && net->ks0 % 2 == 0) ||
+      (net->kind != ET_NET_STACK && net->kind != ET_NET_RESIDUAL) ||
+      (net->kind == ET_NET_RESIDUAL && net->n_layers % 2 == 0))
+    return ET_ERR_ARG;
+  if (st->H < 1 || st->W < 1 || st->H > 65535 || st->W > 65535) return ET_ERR_ARG;
+  if (net->kt > 1 && !st->hist) return ET_ERR_ARG;
+  if (net->C > CP || net->kt > kMaxKt) return ET_ERR_UNIMPLEMENTED;
+  cudaStream_t stream = (cudaStream_t)stream_;
+  const int n = net->n_layers - 1;
+  void* tmp = nullptr;   // event count, then the maxima
+  ET_CHECK_CUDA(cudaMallocAsync(&tmp, sizeof(int64_t) + sizeof(unsigned int) * kMaxLayers, stream));
+  int64_t* n_ev = static_cast<int64_t*>(tmp);
+  unsigned int* amax = reinterpret_cast<unsigned int*>(n_ev + 1);
+  int rc = ET_OK;
+  if (cudaMemsetAsync(tmp, 0, sizeof(int64_t) + sizeof(unsigned int) * kMaxLayers, stream) != cudaSuccess)
+    rc = ET_ERR_CUDA;
+  et_evsnet_weights bf = *net;
+  bf.dtype = ET_BF16;
+  bf.scales = nullptr;
+  if (rc == ET_OK)
+    rc = tct_launch(logl, F, &bf, st, 0, nullptr, 0, n_ev, nullptr, nullptr, false, amax, stream);
+  if (rc == ET_OK) {
+    fp8_scales_kernel<<<1, 32, 0, stream>>>(amax, n_ev, n, headroom, scales);
+    if (cudaGetLastError() != cudaSuccess) rc = ET_ERR_CUDA;
+    else et_count_launch();
+  }
+  if (rc == ET_OK) {
+    const int64_t npix = (int64_t)st->H * st->W;
+    if (cudaMemcpyAsync(st->last_l, logl + (int64_t)(F - 1) * npix, sizeof(float) * npix, cudaMemcpyDeviceToDevice,
+                        stream) != cudaSuccess)
+      rc = ET_ERR_CUDA;
+    else
+      st->initialized = 1;
+  }
+  cudaFreeAsync(tmp, stream);
+  return rc;
 }
