@@ -1,9 +1,9 @@
 // EvSNet forward on the tcgen05 tensor cores for the pixel-wise temporal form:
 // the paper's network (Sec. 4.1, Eq. 5: convolutions of kernel kt along time,
 // plain stack or residual blocks; Eq. 6 projection; BiLIF of Eq. 2-3), with or
-// without a one-step spatial stem as layer 0.  BF16 operands (the weights of
-// layers 1.. and their inputs), FP32 accumulation in TMEM; layer 0, the
-// residual sums, the projection and BiLIF stay FP32.
+// without a one-step spatial stem as layer 0.  BF16 or FP8 (E4M3) operands
+// (the weights of layers 1.. and their inputs), FP32 accumulation in TMEM;
+// layer 0, the residual sums, the projection and BiLIF stay FP32.
 //
 // A CTA owns a tile of 128 consecutive pixels for the whole call: one TMEM
 // lane per pixel and three groups of 128 threads, one thread per pixel each
@@ -50,6 +50,18 @@
 // frame may be the state's, is loaded by the threads.  Layer 0 of chunk
 // tau + 1 is computed in registers while round tau's MMAs run and stored into
 // layer 1's ring after the round's last epilogue.
+//
+// FP8: a layer's MMAs sum taps of several steps, so its input scale is one
+// power of two for the whole call (the caller's calibrated scales), and the
+// weights carry one per output channel.  A ring slot is then 16 bytes per
+// pixel, and one K = 32 MMA covers two consecutive slots (their rows are the
+// two 16-byte columns of the operand); with N = 32 = (step, output channel)
+// its B block holds [[W_i, W_(i-1)], [W_(i+1), W_i]] for the slot pair
+// (i, i + 1), so a layer's two steps take (kt + 2) / 2 MMAs.  The ring is
+// kept twice over (every store also goes R positions on) so that the window's
+// slot pairs never wrap.  The two steps of a pair sum their taps in different
+// orders in both precisions: results depend on a step's place in its pair
+// (FP32 rounding), so calls with even step counts reproduce one call exactly.
 //
 // MMA waits are bounded; on expiry the kernel sets bit 62 of the event count,
 // leaves the membrane and history state untouched, waits (bounded) for its
