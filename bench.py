@@ -243,10 +243,10 @@ def run_reference(args):
 def precision_sweep(api, frames, spp, peaks, n_sm, chunk=250):
     """The precision sweep on its own workload: `frames` + 1 frames of the city
     block at 1280 x 720 and `spp` SPP, rendered once, then EvSNet alone over all
-    of them in every precision the network's form has a kernel for (the trained
-    stem network; the trained 3 x 3 stack, which also has FP8; a random-init
-    3 x 3 stack): device time per frame, throughput against its peak, events,
-    and F1 and EMD against the FP32 output of the same network."""
+    of them in FP32, BF16 and FP8 (the trained stem network, its FP8 input
+    scales calibrated on the first 250 frames; the trained 3 x 3 stack; a
+    random-init 3 x 3 stack): device time per frame, throughput against its
+    peak, events, and F1 and EMD against the FP32 output of the same network."""
     import torch
     from paper_2508_18071_gb300 import inputs
     from paper_2508_18071_gb300 import precision_sweep as ps

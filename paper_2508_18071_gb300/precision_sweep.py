@@ -47,9 +47,10 @@ def macs_per_pixel_step(d: dict) -> int:
     return first + (Ln - 1) * C * C * kt * ks * ks + C
 
 
-def sweep(logl: torch.Tensor, net_d: dict, cap=1 << 20) -> dict:
+def sweep(logl: torch.Tensor, net_d: dict, cap=1 << 20, n_cal=250) -> dict:
     """Each precision the network's form has a kernel for (others are listed
-    as unsupported)."""
+    as unsupported).  FP8 for the pixel-wise form takes per-layer input scales
+    calibrated on the first `n_cal` frames (et_evsnet_fp8_scales, headroom 4)."""
     F, H, W = logl.shape
     K = F - 1
     flops = 2.0 * macs_per_pixel_step(net_d) * H * W * K
@@ -58,6 +59,9 @@ def sweep(logl: torch.Tensor, net_d: dict, cap=1 << 20) -> dict:
     for name, dt in (("f32", L.ET_F32), ("bf16", L.ET_BF16), ("fp8", L.ET_FP8)):
         net = api.EvsNetDev.from_dict(net_d, dt)
         try:
+            if dt == L.ET_FP8 and net.ks == 1:
+                net.scales = api.evsnet_fp8_scales(logl[:min(F, n_cal)].contiguous(), net,
+                                                   api.EvsStateDev(net, H, W))
             api.evsnet_forward(logl[:2].contiguous(), net, api.EvsStateDev(net, H, W), buf=buf)
         except L.ETError as e:
             out[name] = {"unsupported": str(e)}
@@ -77,6 +81,9 @@ def sweep(logl: torch.Tensor, net_d: dict, cap=1 << 20) -> dict:
         loss, _, _ = training.emd_count_loss(S.unsqueeze(0), ref.unsqueeze(0).float(), 0.0)
         out[name] = {"ms_per_frame": ms / K, "tflops": flops / (ms / 1e3) / 1e12, "events": n,
                      "f1_vs_f32": f1, "emd_vs_f32": float(loss[1].item())}
+        if net.scales is not None:
+            out[name]["input_scales"] = net.scales.cpu().tolist()
+            out[name]["calibration"] = "first %d frames, headroom 4" % min(F, n_cal)
         del S
     return out
 
@@ -107,8 +114,8 @@ def main():
 
 def run_nets(logl: torch.Tensor) -> dict:
     """The sweep for the trained city networks (the stem form the benchmark
-    runs, and the four-layer 3x3 stack, whose form also has an FP8 kernel) and
-    a random-init 3x3 stack (N(0, 0.1) weights, Vth 0.5, leak 0.9)."""
+    runs and the four-layer 3x3 stack) and a random-init 3x3 stack (N(0, 0.1)
+    weights, Vth 0.5, leak 0.9)."""
     from . import train_evsnet
     res = {}
     for key, fn in (("trained_stem", "evsnet_city.npz"), ("trained_3x3", "evsnet_city_spatial.npz")):
