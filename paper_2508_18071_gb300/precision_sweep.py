@@ -47,10 +47,10 @@ def macs_per_pixel_step(d: dict) -> int:
     return first + (Ln - 1) * C * C * kt * ks * ks + C
 
 
-def sweep(logl: torch.Tensor, net_d: dict, cap=1 << 20, n_cal=250) -> dict:
+def sweep(logl: torch.Tensor, net_d: dict, cal: torch.Tensor, cap=1 << 20) -> dict:
     """Each precision the network's form has a kernel for (others are listed
     as unsupported).  FP8 for the pixel-wise form takes per-layer input scales
-    calibrated on the first `n_cal` frames (et_evsnet_fp8_scales, headroom 4)."""
+    calibrated on the held-out clip `cal` (et_evsnet_fp8_scales, headroom 4)."""
     F, H, W = logl.shape
     K = F - 1
     flops = 2.0 * macs_per_pixel_step(net_d) * H * W * K
@@ -60,8 +60,7 @@ def sweep(logl: torch.Tensor, net_d: dict, cap=1 << 20, n_cal=250) -> dict:
         net = api.EvsNetDev.from_dict(net_d, dt)
         try:
             if dt == L.ET_FP8 and net.ks == 1:
-                net.scales = api.evsnet_fp8_scales(logl[:min(F, n_cal)].contiguous(), net,
-                                                   api.EvsStateDev(net, H, W))
+                net.scales = api.evsnet_fp8_scales(cal, net, api.EvsStateDev(net, H, W))
             api.evsnet_forward(logl[:2].contiguous(), net, api.EvsStateDev(net, H, W), buf=buf)
         except L.ETError as e:
             out[name] = {"unsupported": str(e)}
@@ -83,7 +82,7 @@ def sweep(logl: torch.Tensor, net_d: dict, cap=1 << 20, n_cal=250) -> dict:
                      "f1_vs_f32": f1, "emd_vs_f32": float(loss[1].item())}
         if net.scales is not None:
             out[name]["input_scales"] = net.scales.cpu().tolist()
-            out[name]["calibration"] = "first %d frames, headroom 4" % min(F, n_cal)
+            out[name]["calibration"] = "held-out clip of %d frames, headroom 4" % cal.shape[0]
         del S
     return out
 
@@ -95,34 +94,40 @@ def main():
     p.add_argument("--width", type=int, default=1280)
     p.add_argument("--height", type=int, default=720)
     p.add_argument("--chunk", type=int, default=200)
+    p.add_argument("--cal-frames", type=int, default=500)
     a = p.parse_args()
     scene = api.Scene(inputs.city_block(seed=21))
-    path = inputs.city_path(a.frames)
-    logl = torch.empty((a.frames, a.height, a.width), dtype=torch.float32, device="cuda")
+    path = inputs.city_path(a.frames + a.cal_frames)
+    n = a.frames + a.cal_frames
+    logl = torch.empty((n, a.height, a.width), dtype=torch.float32, device="cuda")
     t0 = time.time()
-    for f0 in range(0, a.frames, a.chunk):
-        f1 = min(a.frames, f0 + a.chunk)
+    for f0 in range(0, n, a.chunk):
+        f1 = min(n, f0 + a.chunk)
         api.render_frames(scene, path[f0:f1], a.width, a.height, a.spp, 5, 0, first_frame=f0,
                           logl=logl[f0:f1], want_rgb=False)
     torch.cuda.synchronize()
+    cal = logl[a.frames:].contiguous()
+    logl = logl[:a.frames]
     res = {"workload": "city block 500k triangles, %dx%d, %d frames at 1 kHz, %d SPP, depth 5"
                        % (a.width, a.height, a.frames, a.spp),
            "render_s": time.time() - t0}
-    res.update(run_nets(logl))
+    res.update(run_nets(logl, cal))
     print(json.dumps(res))
 
 
-def run_nets(logl: torch.Tensor) -> dict:
+def run_nets(logl: torch.Tensor, cal: torch.Tensor) -> dict:
     """The sweep for the trained city networks (the stem form the benchmark
     runs and the four-layer 3x3 stack) and a random-init 3x3 stack (N(0, 0.1)
-    weights, Vth 0.5, leak 0.9)."""
+    weights, Vth 0.5, leak 0.9); `cal`: the held-out calibration clip of the
+    FP8 input scales (the frames after the swept ones on the same path)."""
     from . import train_evsnet
     res = {}
     for key, fn in (("trained_stem", "evsnet_city.npz"), ("trained_3x3", "evsnet_city_spatial.npz")):
         path = os.path.join(HERE, "weights", fn)
         if os.path.exists(path):
-            res[key] = sweep(logl, train_evsnet.load(path))
-    res["random_init_3x3"] = sweep(logl, inputs.random_evsnet(0, 4, 16, 1, 3, seed=12, vth=0.5, beta=0.9))
+            res[key] = sweep(logl, train_evsnet.load(path), cal)
+    res["random_init_3x3"] = sweep(logl, inputs.random_evsnet(0, 4, 16, 1, 3, seed=12, vth=0.5, beta=0.9),
+                                   cal)
     return res
 
 
