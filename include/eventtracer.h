@@ -197,6 +197,15 @@ enum { ET_RENDER_WAVEFRONT = 0, ET_RENDER_MEGAKERNEL = 1, ET_RENDER_WAVEFRONT_TI
        ET_RENDER_WAVEFRONT_SORTED = 3 };
 int et_render_set_mode(et_scene* scene, int32_t mode);
 
+/* The counter-based generator behind every random number of the renderer
+ * (camera jitter, light and BSDF samples; Sec. 3.2's Monte Carlo estimator)
+ * and of the sensor model: Philox4x32-10 (Salmon et al., SC'11), evaluated on
+ * the device for caller counters and keys, for testing it bit for bit.
+ *   ctr  device uint32 [n][4] (16-byte aligned), key device uint32 [n][2]
+ *   (8-byte aligned), out device uint32 [n][4] (16-byte aligned).
+ * Errors: ET_ERR_ARG (null or misaligned buffers, n < 0), ET_ERR_CUDA. */
+int et_philox4x32_10(const uint32_t* ctr, const uint32_t* key, int64_t n, uint32_t* out, void* stream);
+
 /* Per-kernel device time of the wavefront schedule, for measurement (not part
  * of the method).  et_render_profile(scene, 1): every later et_render_frames
  * call on this scene records a CUDA event before and after each of its

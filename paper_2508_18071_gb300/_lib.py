@@ -74,6 +74,7 @@ SIGNATURES = {
     "et_threshold_events": (i32, [P, i32, i32, i32, f32, i32, P, i32, P, i64, P, P]),
     "et_evsnet_forward": (i32, [P, i32, P, P, i32, P, i64, P, P, P, P]),
     "et_evsnet_fp8_scales": (i32, [P, i32, P, P, f32, P, P]),
+    "et_philox4x32_10": (i32, [P, P, i64, P, P]),
     "et_train_workspace_bytes": (i32, [P, P, P]),
     "et_evsnet_train_forward": (i32, [P, P, P, P, P, P, P, P, P, C.c_size_t, P]),
     "et_emd_count_loss": (i32, [P, P, P, f32, P, P, P, P]),

@@ -347,6 +347,16 @@ def sensor_events(logl: torch.Tensor, prm: SensorParams, state: SensorStateDev, 
     return buf
 
 
+def philox4x32_10(ctr: torch.Tensor, key: torch.Tensor, stream=None) -> torch.Tensor:
+    """et_philox4x32_10: the device generator on counters [n, 4] and keys [n, 2]
+    (uint32 values held in int32 device tensors); returns [n, 4]."""
+    ctr, key = ctr.contiguous(), key.contiguous()
+    out = torch.empty_like(ctr)
+    st = L.load().et_philox4x32_10(_ptr(ctr), _ptr(key), ctr.shape[0], _ptr(out), _stream(stream))
+    L.check("et_philox4x32_10", st)
+    return out
+
+
 # ------------------------------------------------------------------ EvSNet
 @dataclass
 class EvsNetDev:

@@ -211,3 +211,32 @@ extern "C" int et_render_set_mode(et_scene* scene, int32_t mode) {
   scene->render_mode = mode;
   return ET_OK;
 }
+
+// ------------------------------------------------------------------ Philox
+namespace {
+
+__global__ void philox_kernel(const uint4* ctr, const uint2* key, int64_t n, uint4* out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint4 c = ctr[i];
+  const uint2 k = key[i];
+  const u4 r = philox10(c.x, c.y, c.z, c.w, k.x, k.y);
+  out[i] = make_uint4(r.x, r.y, r.z, r.w);
+}
+
+}  // namespace
+
+// The renderer's and the sensor model's counter-based generator, evaluated on
+// caller counters (the bitwise pin of the device Philox4x32-10).
+extern "C" int et_philox4x32_10(const uint32_t* ctr, const uint32_t* key, int64_t n, uint32_t* out,
+                                void* stream) {
+  if (n < 0 || (n > 0 && (!ctr || !key || !out))) return ET_ERR_ARG;
+  if ((reinterpret_cast<uintptr_t>(ctr) & 15) || (reinterpret_cast<uintptr_t>(out) & 15) ||
+      (reinterpret_cast<uintptr_t>(key) & 7))
+    return ET_ERR_ARG;
+  if (n == 0) return ET_OK;
+  philox_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+      reinterpret_cast<const uint4*>(ctr), reinterpret_cast<const uint2*>(key), n, reinterpret_cast<uint4*>(out));
+  ET_CHECK_LAUNCH();
+  return ET_OK;
+}
