@@ -10,7 +10,8 @@
 // (warps w, w + 4, w + 8 share TMEM lane quarter w); group g runs the
 // epilogues of every third tensor-core layer counting down from the last, so
 // that consecutive layers' epilogues run at once in different warps; group 1
-// also runs layer 0, group 0 the projection and BiLIF.  A thirteenth warp's
+// also runs layer 0 (FP8: groups 1 and 2, 8 channels each), group 0 the
+// projection and BiLIF.  A thirteenth warp's
 // one thread issues every MMA and TMA copy, so that issuing never holds up
 // the epilogues.  The input history of every layer >= 1 (its
 // last kt inputs) lives in shared memory as a ring of kt + kT - 1 slots, each
@@ -242,6 +243,13 @@ evsnet_tct_kernel(const __grid_constant__ CUtensorMap tmap, TctParams P, const f
   const int64_t q = (int64_t)blockIdx.x * TP + p;
   const bool worker = tid < kWorkers;
   const bool stem_grp = grp == kStemGroup;
+  // layer 0: the stem group alone (BF16), or split by channel halves between
+  // groups 1 and 2 (FP8: its shorter MMA stream leaves layer 0 on the round's
+  // critical path); the X ring of a temporal layer 0 is then written by both,
+  // each with the value it reads back itself
+  constexpr int kSC = kF8 ? CP / 2 : CP;          // layer-0 channels per participating thread
+  const bool stem_part = kF8 ? (grp == 1 || grp == 2) : stem_grp;
+  const int c_lo = (kF8 && grp == 2) ? CP / 2 : 0;   // its first channel
   const bool live = worker && q < npix;
   const int px = live ? (int)(q % P.W) : 0, py = live ? (int)(q / P.W) : 0;
   constexpr int kSB = kF8 ? kSlot8 : kSlot;                    // bytes per ring slot
@@ -421,7 +429,7 @@ evsnet_tct_kernel(const __grid_constant__ CUtensorMap tmap, TctParams P, const f
       }
     }
   };
-  if (ks0 == 3 && stem_grp) load_x9(0);
+  if (ks0 == 3 && stem_part) load_x9(0);
   // TMA of the stem's input: the tile's row segment (tiles are whole row
   // segments when it is used), one box per chunk, two buffers
   const int tx0 = (int)(((int64_t)blockIdx.x * TP) % P.W), ty0 = (int)(((int64_t)blockIdx.x * TP) / P.W);
@@ -437,9 +445,9 @@ evsnet_tct_kernel(const __grid_constant__ CUtensorMap tmap, TctParams P, const f
   // (Eq. 1); the 3 x 3 stem reads its neighbours' X from xn (thread loads) or
   // from the chunk's TMA box.  The FP32 output goes to TMEM at once (the first
   // residual block's input), the BF16-rounded one waits in h0p for layer 1's ring
-  uint32_t h0p[kT][kF8 ? CP / 4 : CP / 2];
+  uint32_t h0p[kT][kF8 ? kSC / 4 : CP / 2];
   auto stem = [&](int ch) {
-    float h0n[kT][CP];
+    float h0n[kT][kSC];
     const int s0 = ch * kT, tc = min(kT, S - s0);
     if (P.tma && ch > 0) {
       const int b = ch & 1;
@@ -460,19 +468,19 @@ evsnet_tct_kernel(const __grid_constant__ CUtensorMap tmap, TctParams P, const f
 #pragma unroll
     for (int j = 0; j < kT; ++j) {
 #pragma unroll
-      for (int c = 0; c < CP; ++c) h0n[j][c] = 0.0f;
+      for (int c = 0; c < kSC; ++c) h0n[j][c] = 0.0f;
       if (j >= tc) continue;
       const int f = P.f0 + s0 + j;
-      float acc[CP];
+      float acc[kSC];
 #pragma unroll
-      for (int c = 0; c < CP; ++c) acc[c] = bs[c];
+      for (int c = 0; c < kSC; ++c) acc[c] = bs[c_lo + c];
       if (live) {
         if (ks0 == 3) {
 #pragma unroll
           for (int t = 0; t < 9; ++t) {
-            const float* wt = w0 + t * CP;
+            const float* wt = w0 + t * CP + c_lo;
 #pragma unroll
-            for (int c = 0; c < CP; ++c) acc[c] = fmaf(wt[c], xn[j][t], acc[c]);
+            for (int c = 0; c < kSC; ++c) acc[c] = fmaf(wt[c], xn[j][t], acc[c]);
           }
         } else if (ks0 > 0) {
           const int r0 = ks0 >> 1;
@@ -486,9 +494,9 @@ evsnet_tct_kernel(const __grid_constant__ CUtensorMap tmap, TctParams P, const f
               const float xc = __ldg(logl + (int64_t)f * npix + qq);
               const float xp = f == 0 ? last_l[qq] : __ldg(logl + (int64_t)(f - 1) * npix + qq);
               const float v = xc - xp;
-              const float* wt = w0 + (dy * ks0 + dx) * CP;
+              const float* wt = w0 + (dy * ks0 + dx) * CP + c_lo;
 #pragma unroll
-              for (int c = 0; c < CP; ++c) acc[c] = fmaf(wt[c], v, acc[c]);
+              for (int c = 0; c < kSC; ++c) acc[c] = fmaf(wt[c], v, acc[c]);
             }
           }
         } else {
@@ -497,22 +505,26 @@ evsnet_tct_kernel(const __grid_constant__ CUtensorMap tmap, TctParams P, const f
           xh[ring_pos(s0 + j, R) * TP + p] = xc - xp;
           for (int tau0 = 0; tau0 < kt; ++tau0) {
             const float v = xh[ring_pos(s0 + j - hk + tau0, R) * TP + p];
-            const float* wt = w0 + tau0 * CP;
+            const float* wt = w0 + tau0 * CP + c_lo;
 #pragma unroll
-            for (int c = 0; c < CP; ++c) acc[c] = fmaf(wt[c], v, acc[c]);
+            for (int c = 0; c < kSC; ++c) acc[c] = fmaf(wt[c], v, acc[c]);
           }
         }
       }
 #pragma unroll
-      for (int c = 0; c < CP; ++c) h0n[j][c] = live ? fmaxf(acc[c], 0.0f) : 0.0f;
+      for (int c = 0; c < kSC; ++c) h0n[j][c] = live ? fmaxf(acc[c], 0.0f) : 0.0f;
     }
-    if (residual && L >= 3) tmem_st32(hb_col(0, ch), &h0n[0][0]);
+    if (residual && L >= 3) {
+      // the first block's FP32 input: columns (step j, channel c) = 16 j + c
+      if constexpr (kSC == CP) tmem_st32(hb_col(0, ch), &h0n[0][0]);
+      else tmem_st8x2(hb_col(0, ch) + c_lo, hb_col(0, ch) + CP + c_lo, h0n[0], h0n[1]);
+    }
     if (kCal) {
       float m = 0.0f;
 #pragma unroll
       for (int j = 0; j < kT; ++j)
 #pragma unroll
-        for (int c = 0; c < CP; ++c) m = fmaxf(m, h0n[j][c]);
+        for (int c = 0; c < kSC; ++c) m = fmaxf(m, h0n[j][c]);
       const unsigned r = __reduce_max_sync(0xFFFFFFFFu, __float_as_uint(m));
       if (lane == 0) atomicMax(P.amax, r);
     }
@@ -521,7 +533,7 @@ evsnet_tct_kernel(const __grid_constant__ CUtensorMap tmap, TctParams P, const f
       if constexpr (kF8) {
         const float inv = isc[1];
 #pragma unroll
-        for (int c = 0; c < CP / 4; ++c)
+        for (int c = 0; c < kSC / 4; ++c)
           h0p[j][c] = pack_e4m3(h0n[j][4 * c] * inv, h0n[j][4 * c + 1] * inv, h0n[j][4 * c + 2] * inv,
                                 h0n[j][4 * c + 3] * inv);
       } else {
@@ -538,20 +550,22 @@ evsnet_tct_kernel(const __grid_constant__ CUtensorMap tmap, TctParams P, const f
       if (j >= tc) break;
       const int pos = pc + j >= R ? pc + j - R : pc + j;
       unsigned char* slot = slot_of(1, pos);
-      *reinterpret_cast<uint4*>(slot + p * 16) = make_uint4(h0p[j][0], h0p[j][1], h0p[j][2], h0p[j][3]);
       if constexpr (kF8) {
+        // this thread's 8 channels: 8 bytes of the 16-byte row
+        *reinterpret_cast<uint2*>(slot + p * 16 + c_lo) = make_uint2(h0p[j][0], h0p[j][1]);
         if (pos + R < RS)
-          *reinterpret_cast<uint4*>(slot_of(1, pos + R) + p * 16) = make_uint4(h0p[j][0], h0p[j][1], h0p[j][2], h0p[j][3]);
-      }
-      else
+          *reinterpret_cast<uint2*>(slot_of(1, pos + R) + p * 16 + c_lo) = make_uint2(h0p[j][0], h0p[j][1]);
+      } else {
+        *reinterpret_cast<uint4*>(slot + p * 16) = make_uint4(h0p[j][0], h0p[j][1], h0p[j][2], h0p[j][3]);
         *reinterpret_cast<uint4*>(slot + kPlane + p * 16) =
             make_uint4(h0p[j][4], h0p[j][5], h0p[j][6], h0p[j][7]);
+      }
     }
   };
   // chunk 0 before the first round (its previous frame may be the state's:
   // thread loads), chunk 1's box in flight
   if (tid == kIssuer && P.tma && nch > 1) issue_box(1);
-  if (stem_grp && nch > 0) {
+  if (stem_part && nch > 0) {
     stem(0);
     stem_store(0);
     if (ks0 == 3 && !P.tma) load_x9(kT);
@@ -625,7 +639,7 @@ evsnet_tct_kernel(const __grid_constant__ CUtensorMap tmap, TctParams P, const f
       }
     }
     // ---- layer 0 of the next chunk, in registers, while the MMAs run
-    if (stem_grp && tau + 1 < nch) {
+    if (stem_part && tau + 1 < nch) {
       stem(tau + 1);
       if (ks0 == 3 && !P.tma) load_x9((tau + 2) * kT);   // consumed next round
     }
@@ -702,7 +716,7 @@ evsnet_tct_kernel(const __grid_constant__ CUtensorMap tmap, TctParams P, const f
     }
     // layer 1's MMAs of this round are complete once its commit has arrived:
     // chunk tau + 1 may then overwrite the ring slots they read
-    if (stem_grp && tau + 1 < nch) {
+    if (stem_part && tau + 1 < nch) {
       if (!owns(1)) {
         if (!mbar_wait(&lbar[1], (lphase >> 1) & 1u, P.wait_iters)) {
           if (lane == 0) atomicOr(n_events, kTimeoutBit);
